@@ -1,0 +1,275 @@
+/*
+ * fcoo.h -- C ABI of libfcoo.so, a GB300 (sm_103a) implementation of the
+ * F-COO sparse tensor kernels of "A Unified Optimization Approach for Sparse
+ * Tensor Operations on GPUs" (Liu, Wen, Sarwate, Mehri Dehnavi, 2017).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Tensors are N-way (2 <= N <= FCOO_MAX_MODES) coordinate lists with
+ *    0-based indices (the paper is 1-based, Sec. II).  Index arrays are
+ *    uint32, one per mode; values are float32.
+ *  - Dense matrices (factor matrices, U, outputs) are row-major with R
+ *    contiguous columns per row: element (i, r) lives at ptr[i * R + r].
+ *    Device pointers must be 16-byte aligned.
+ *  - "host or device" pointers are classified with cudaPointerGetAttributes;
+ *    everything else named "device" must be device memory of the current
+ *    device.  Nothing is retained after a call returns except inside the
+ *    opaque handles, which own their device memory.
+ *  - Streams are cudaStream_t values (NULL = legacy default stream).  Compute
+ *    entry points are asynchronous on that stream unless documented as
+ *    synchronous; argument errors are reported synchronously, kernel errors by
+ *    the next synchronous call.
+ *  - Every entry point returns FCOO_OK (0) or a negative status; the calling
+ *    thread's last error message is available from fcoo_last_error().  No
+ *    entry point aborts, traps or prints.
+ *  - A handle must not be used by two calls that overlap on the GPU (the
+ *    kernels share the handle's scratch memory); issue them on one stream.
+ */
+#ifndef FCOO_H
+#define FCOO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FCOO_MAX_MODES 8
+/* Largest rank (columns R) the kernels accept. */
+#define FCOO_MAX_RANK 256
+/* Largest number of nonzeros one handle holds. */
+#define FCOO_MAX_NNZ 2147479552LL
+
+typedef struct CUstream_st *fcoo_stream_t; /* same type as cudaStream_t */
+typedef struct fcoo fcoo_t;
+typedef struct cp_state cp_state_t;
+
+typedef enum { FCOO_F32 = 0, FCOO_BF16 = 1 } fcoo_dtype;
+
+/* Table I: which modes are product modes and which are index modes. */
+typedef enum { FCOO_OP_MTTKRP = 0, FCOO_OP_TTM = 1 } fcoo_op;
+
+enum {
+    FCOO_OK = 0,
+    FCOO_ERR_INVALID_ARG = -1, /* bad pointer, size, mode, rank, dtype, ...   */
+    FCOO_ERR_INDEX_RANGE = -2, /* an index >= its dimension                    */
+    FCOO_ERR_DUPLICATE = -3,   /* two nonzeros with identical coordinates      */
+    FCOO_ERR_NOMEM = -4,       /* a device or host allocation failed           */
+    FCOO_ERR_CUDA = -5,        /* a CUDA runtime call failed                   */
+    FCOO_ERR_NOT_PD = -6,      /* normal equations could not be solved         */
+    FCOO_ERR_NONFINITE = -7,   /* NaN or Inf met where a finite value is needed */
+    FCOO_ERR_TIMEOUT = -8,     /* a bounded device wait gave up                */
+    FCOO_ERR_UNSUPPORTED = -9  /* valid request outside this build's limits    */
+};
+
+/* Description of a built F-COO handle (fcoo_info). */
+typedef struct {
+    int nmodes, mode, op, threadlen;
+    int64_t nnz;
+    int64_t nseg;  /* index-mode tuples = output rows written (SpMTTKRP) or fibres (SpTTM) */
+    int64_t nfib;  /* distinct (index modes, all product modes but the last) tuples */
+    uint32_t dims[FCOO_MAX_MODES];
+    int nprod, prod_modes[FCOO_MAX_MODES]; /* product modes, in stream order (Table I) */
+    int nidx, idx_modes[FCOO_MAX_MODES];   /* index modes, in sort order (Table I)     */
+    /* Table II terms: val (4 B/nnz), product-mode indices (4 B/nnz each),
+     * bit-flags (1 bit/nnz, packed in 32-bit words) and start-flags (1 bit per
+     * partition of threadlen nonzeros, packed in 32-bit words). */
+    int64_t bytes_val, bytes_pidx, bytes_bf, bytes_sf;
+    int64_t bytes_table2;  /* sum of the four terms above                   */
+    int64_t bytes_segmap;  /* segment -> output row / fibre index tuples     */
+    int64_t bytes_aux;     /* segment counts per 1024 nonzeros, permutation  */
+    int64_t bytes_scratch; /* carry buffers used by the kernels              */
+} fcoo_info_t;
+
+/* ---------------------------------------------------------------------- */
+/* Library                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Message describing the calling thread's most recent failure ("" if none).
+ * The pointer stays valid until the thread's next failing call. */
+const char *fcoo_last_error(void);
+
+/* Static name of a status code. */
+const char *fcoo_status_string(int status);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int fcoo_version(void);
+
+/* Host-only: bytes of the four Table II arrays that fcoo_build allocates for
+ * a tensor with `nprod` product modes (Table II; nprod = 2 for 3-way
+ * SpMTTKRP, 1 for SpTTM): 4*nnz (val) + 4*nprod*nnz (indices) +
+ * 4*ceil(nnz/32) (bf) + 4*ceil(ceil(nnz/threadlen)/32) (sf).  For nnz a
+ * multiple of 32*threadlen this is exactly (4 + 4*nprod + 1/8 +
+ * 1/(8*threadlen)) * nnz.  Returns -1 on bad arguments. */
+int64_t fcoo_table2_bytes(int nprod, int64_t nnz, int threadlen);
+
+/* ---------------------------------------------------------------------- */
+/* F-COO construction (Sec. IV-B, Table I, Table II, Fig. 2; host          */
+/* preprocessing of Sec. IV-D "Complete tensor-based algorithms")          */
+/* ---------------------------------------------------------------------- */
+
+/* Build the F-COO form of an N-way COO tensor for one operation on one
+ * mode, on the GPU:
+ *   - op = FCOO_OP_MTTKRP: index mode = `mode`, product modes = all others
+ *     in ascending order;  op = FCOO_OP_TTM: product mode = `mode`, index
+ *     modes = all others in ascending order (Table I);
+ *   - nonzeros are sorted lexicographically by (index modes, product modes);
+ *   - the stream holds, per nonzero, the product-mode indices and the value
+ *     (Table II); the bit-flag array marks with a 1 every nonzero that starts
+ *     a new index-mode tuple (a new slice for SpMTTKRP, a new fibre for
+ *     SpTTM; the paper's toggling bit changes at exactly these positions,
+ *     Fig. 2); the start-flag array holds one bit per partition of
+ *     `threadlen` nonzeros, set when the partition starts a new tuple;
+ *   - the index-mode tuple of each segment is kept (the output row of an
+ *     SpMTTKRP segment, the fibre index of an SpTTM output fibre), so slices
+ *     without nonzeros are allowed.
+ * Arguments:
+ *   nmodes    N, 2..FCOO_MAX_MODES
+ *   dims      host array of N dimensions, each >= 1
+ *   nnz       0..FCOO_MAX_NNZ
+ *   idx       host array of N pointers (host or device), idx[k][p] < dims[k]
+ *   val       nnz values (host or device)
+ *   mode      0..N-1
+ *   op        FCOO_OP_MTTKRP or FCOO_OP_TTM
+ *   threadlen nonzeros per partition, a power of two 1..64 (the paper packs
+ *             the flags of one partition in a uint8..uint64: 8..64; Fig. 2
+ *             illustrates 4)
+ *   stream    stream for the device work
+ *   out       receives the handle (NULL on failure)
+ * The inputs are copied; the caller keeps ownership.  Synchronous: the
+ * stream is synchronised before return.  Errors: FCOO_ERR_INVALID_ARG,
+ * FCOO_ERR_INDEX_RANGE, FCOO_ERR_DUPLICATE, FCOO_ERR_NOMEM, FCOO_ERR_CUDA.
+ * Environment FCOO_FAULT_ALLOC=k makes the k-th device allocation of the
+ * process fail (test hook; k counts from 1). */
+int fcoo_build(int nmodes, const uint32_t *dims, int64_t nnz, const uint32_t *const *idx, const float *val,
+               int mode, int op, int threadlen, fcoo_stream_t stream, fcoo_t **out);
+
+/* Free a handle and its device memory (NULL is accepted).  Synchronises the
+ * device first so that no kernel still reads the handle. */
+int fcoo_destroy(fcoo_t *X);
+
+/* Fill *info (host struct) from the handle.  Host only, no device work. */
+int fcoo_info(const fcoo_t *X, fcoo_info_t *info);
+
+/* Copy parts of the layout to host buffers (any may be NULL).  Synchronous.
+ *   perm     nnz uint32: original COO position of the q-th nonzero in F-COO order
+ *   bf       ceil(nnz/32) uint32 words, bit (p % 32) of word p/32 = flag of nonzero p
+ *   sf       ceil(ceil(nnz/threadlen)/32) uint32 words, bit t%32 of word t/32
+ *   segkeys  nseg * nidx uint32: index-mode tuple of each segment
+ *   pidx     nprod * nnz uint32: product-mode index streams, one after the other
+ *   val      nnz float32 values in F-COO order */
+int fcoo_copy_layout(const fcoo_t *X, uint32_t *perm, uint32_t *bf, uint32_t *sf, uint32_t *segkeys,
+                     uint32_t *pidx, float *val, fcoo_stream_t stream);
+
+/* Index tuples of the SpTTM output fibres (the semi-sparse result of Eq. 3,
+ * Sec. II): nseg rows of (N-1) uint32, in output-row order, written to host
+ * or device memory `keys`.  Synchronous.  For an SpMTTKRP handle it returns
+ * the output row of each segment (nseg values). */
+int fcoo_fibre_indices(const fcoo_t *X, uint32_t *keys, fcoo_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* SpMTTKRP (Eq. 5, Eq. 6, Table I row 2; one-shot product of Sec. IV-C;    */
+/* segmented reduction of Sec. IV-D)                                        */
+/* ---------------------------------------------------------------------- */
+
+/* out(i, :) = sum over nonzeros p with idx_mode(p) = i of
+ *             val(p) * prod_{k != mode} F_k(idx_k(p), :)
+ * X        handle built with op = FCOO_OP_MTTKRP
+ * factors  host array of N device pointers; factors[k] is dims[k] x R of
+ *          dtype (FCOO_F32 or FCOO_BF16); factors[mode] is not read (may be NULL)
+ * R        1..FCOO_MAX_RANK
+ * out      device float32 dims[mode] x R; every element is written (rows
+ *          without nonzeros are set to 0); no pre-zeroing needed
+ * The reduction order is fixed by the handle and R, so repeated calls give
+ * bitwise identical results.  Asynchronous on `stream`. */
+int spmttkrp(const fcoo_t *X, const void *const *factors, int dtype, int R, float *out, fcoo_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* SpTTM (Eq. 3, Table I row 1; semi-sparse output of Sec. II)              */
+/* ---------------------------------------------------------------------- */
+
+/* Y(f, :) = sum over nonzeros p in output fibre f of val(p) * U(idx_mode(p), :)
+ * X    handle built with op = FCOO_OP_TTM
+ * U    device dims[mode] x R of dtype
+ * out  device float32 nseg x R; row f is the fibre whose index tuple is row f
+ *      of fcoo_fibre_indices (lexicographic order); every element written.
+ * Asynchronous on `stream`. */
+int spttm(const fcoo_t *X, const void *U, int dtype, int R, float *out, fcoo_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* CP-ALS (Algorithm 1; Sec. IV-D "Complete tensor-based algorithms")       */
+/* ---------------------------------------------------------------------- */
+
+/* Create the device state of a rank-R CP decomposition: factor matrices
+ * stored as dtype (FCOO_F32 or FCOO_BF16), lambda, FP64 Gram matrices,
+ * the last MTTKRP, iteration count and fit.
+ *   init  host array of N pointers (host or device) to float32 dims[k] x R
+ *         initial factors (rounded to dtype on copy).
+ * Synchronous. */
+int cp_state_create(int nmodes, const uint32_t *dims, int R, int dtype, const float *const *init,
+                    fcoo_stream_t stream, cp_state_t **out);
+int cp_state_destroy(cp_state_t *st);
+
+/* One full sweep of Algorithm 1 over all modes n = 0..N-1:
+ *   M   = SpMTTKRP_n(X, F)                       (Eq. 6, FP32 accumulation)
+ *   V   = Hadamard product over k != n of F_k^T F_k  (Grams in FP64)
+ *   F_n = M V^dagger   (FP64 Cholesky; if a pivot is <= 1e-12 * max diag(V),
+ *                       the eigen-decomposition pseudo-inverse that drops
+ *                       eigenvalues <= 1e-12 * max |eig|)
+ *   lambda = column 2-norms of F_n; F_n columns divided by them (a zero
+ *            column keeps lambda 0 and is left as it is)
+ * then the fit 1 - sqrt(max(0, |X|^2 + |Xhat|^2 - 2<X,Xhat>)) / |X|.
+ *   Xn  host array of N handles, Xn[n] built with op = FCOO_OP_MTTKRP, mode n,
+ *       all from the same tensor.
+ * Asynchronous on `stream`; read results with cp_state_stats. */
+int cp_als_iter(const fcoo_t *const *Xn, cp_state_t *st, fcoo_stream_t stream);
+
+/* Synchronous read of lambda (host, R doubles, may be NULL), the last fit,
+ * the number of completed sweeps and the number of pseudo-inverse solves. */
+int cp_state_stats(const cp_state_t *st, double *lambda, double *fit, int *iters, int *npinv, fcoo_stream_t stream);
+
+/* Copy factor k as float32 (dims[k] x R) to host or device memory. Synchronous. */
+int cp_state_copy_factor(const cp_state_t *st, int k, float *dst, fcoo_stream_t stream);
+
+/* Checkpoint: size of the blob, serialise to host memory, restore from it
+ * (same nmodes, dims, R and dtype).  Synchronous. */
+int64_t cp_state_blob_size(const cp_state_t *st);
+int cp_state_save(const cp_state_t *st, void *blob, int64_t size, fcoo_stream_t stream);
+int cp_state_load(cp_state_t *st, const void *blob, int64_t size, fcoo_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
+/* Differentiation: loss and adjoints built from the Eq. 6 one-shot product */
+/* ---------------------------------------------------------------------- */
+
+/* kind = 0, sparse CP fit over the observed entries:
+ *   e(p) = sum_r prod_k F_k(idx_k(p), r) - val(p),  loss = 1/2 sum_p e(p)^2
+ *   dfactors[n](i, :) = sum_{p: idx_n(p) = i} e(p) prod_{k != n} F_k(idx_k(p), :)
+ *   dvals(p) = -e(p), in the caller's original COO order
+ *   Xn: N handles (op MTTKRP, mode n each); `mode` and gradM are ignored;
+ *   loss: device double (may be NULL); dfactors[n] device float32 dims[n] x R
+ *   (entries may be NULL to skip that mode); dvals device float32 nnz (may be NULL).
+ * kind = 1, adjoint of M = SpMTTKRP_mode(X, F) for gradM = dL/dM (device
+ * float32 dims[mode] x R):
+ *   dfactors[k](j, :) = sum_{p: idx_k(p) = j} val(p) gradM(idx_mode(p), :)
+ *                       * prod_{m != mode, k} F_m(idx_m(p), :)     (k != mode)
+ *   dvals(p) = sum_r gradM(idx_mode(p), r) prod_{k != mode} F_k(idx_k(p), r)
+ *   Xn: N handles as above (Xn[k] is used for dfactors[k]); dvals uses Xn[mode].
+ * All outputs are fully overwritten.  Asynchronous on `stream`. */
+int spmttkrp_backward(const fcoo_t *const *Xn, const void *const *factors, int dtype, int R, const float *gradM,
+                      int kind, int mode, float *const *dfactors, float *dvals, double *loss, fcoo_stream_t stream);
+
+/* Forward value of the kind = 0 loss only (device double *loss). */
+int sparse_cp_loss(const fcoo_t *X, const void *const *factors, int dtype, int R, double *loss,
+                   fcoo_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+#endif /* FCOO_H */

@@ -222,3 +222,32 @@ def mttkrp_adjoint(dims, idx, val, factors, mode, G):
                                   val.ctypes.data_as(_f64p), _ptr_table(fs), R, mode, G.ctypes.data_as(_f64p),
                                   _ptr_table(dfs), dv.ctypes.data_as(_f64p)))
     return dfs, dv
+
+
+def cp_als_mode(dims, idx, val, factors, n):
+    """One mode update of Algorithm 1 (in place on a copy).  Returns
+    (factors, lambda, M, used_pinv)."""
+    lib = _load()
+    lib.orc_cp_als_mode.restype = ctypes.c_int
+    c = _Coo(dims, idx)
+    val = _f64(val)
+    fs = [_f64(f).copy() for f in factors]
+    R = int(fs[0].shape[1])
+    lam = np.empty(R, dtype=np.float64)
+    M = np.empty((int(c.dims[n]), R), dtype=np.float64)
+    used = _check(lib.orc_cp_als_mode(c.nmodes, c.dims_ptr, ctypes.c_int64(c.nnz), c.idx_ptrs,
+                                      val.ctypes.data_as(_f64p), R, n, _ptr_table(fs), lam.ctypes.data_as(_f64p),
+                                      M.ctypes.data_as(_f64p)))
+    return fs, lam, M, bool(used)
+
+
+def cp_fit(dims, idx, val, factors, lam):
+    """Fit 1 - |X - [lambda; F]| / |X| of Algorithm 1's model (Grams identity)."""
+    lib = _load()
+    lib.orc_cp_fit.restype = ctypes.c_double
+    c = _Coo(dims, idx)
+    val = _f64(val)
+    fs = [_f64(f) for f in factors]
+    lam = _f64(lam)
+    return float(lib.orc_cp_fit(c.nmodes, c.dims_ptr, ctypes.c_int64(c.nnz), c.idx_ptrs, val.ctypes.data_as(_f64p),
+                                int(fs[0].shape[1]), _ptr_table(fs), lam.ctypes.data_as(_f64p)))

@@ -480,3 +480,78 @@ int orc_mttkrp_adjoint(int nmodes, const uint32_t *dims, int64_t nnz, const uint
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 split into its steps, for checking a device path that rounds  */
+/* the factors between steps.                                                 */
+/* One mode update of the loop body, for mode n:                             */
+/*   V = Hadamard_{k != n} F_k^T F_k;  F_n = MTTKRP_n(X, F) V^dagger;         */
+/*   lambda = column 2-norms of F_n; F_n columns divided by them.            */
+/* M_out (may be NULL) receives the MTTKRP.  Returns 1 if the                 */
+/* pseudo-inverse was used, 0 for Cholesky, < 0 on error.                     */
+/* ------------------------------------------------------------------------ */
+int orc_cp_als_mode(int nmodes, const uint32_t *dims, int64_t nnz, const uint32_t *const *idx,
+                    const double *val, int R, int n, double *const *factors, double *lambda, double *M_out)
+{
+    int st = check_coo(nmodes, dims, nnz, idx);
+    if (st) return st;
+    if (R <= 0 || n < 0 || n >= nmodes) return ORC_ERR_ARG;
+    double *M = (double *)malloc(sizeof(double) * (size_t)dims[n] * R);
+    double *V = (double *)malloc(sizeof(double) * (size_t)R * R);
+    double *G = (double *)malloc(sizeof(double) * (size_t)R * R);
+    orc_mttkrp(nmodes, dims, nnz, idx, val, (const double *const *)factors, R, n, M);
+    for (int a = 0; a < R * R; ++a) V[a] = 1.0;
+    for (int k = 0; k < nmodes; ++k) {
+        if (k == n) continue;
+        orc_gram(factors[k], dims[k], R, G);
+        for (int a = 0; a < R * R; ++a) V[a] *= G[a];
+    }
+    int used = orc_spd_solve(V, R, M, dims[n], factors[n]);
+    for (int r = 0; r < R; ++r) {
+        double s = 0.0;
+        for (uint32_t i = 0; i < dims[n]; ++i) s += factors[n][(size_t)i * R + r] * factors[n][(size_t)i * R + r];
+        double nr = sqrt(s);
+        lambda[r] = nr;
+        if (nr > 0.0)
+            for (uint32_t i = 0; i < dims[n]; ++i) factors[n][(size_t)i * R + r] /= nr;
+    }
+    if (M_out) memcpy(M_out, M, sizeof(double) * (size_t)dims[n] * R);
+    free(M);
+    free(V);
+    free(G);
+    return used;
+}
+
+/* The fit of Algorithm 1's model [lambda; F_0..F_{N-1}] against X, from the  */
+/* definition 1 - |X - Xhat| / |X| with                                       */
+/* |X - Xhat|^2 = |X|^2 + lambda^T (Hadamard_k F_k^T F_k) lambda              */
+/*                - 2 sum_r lambda_r sum_i M_last(i,r) F_last(i,r),           */
+/* M_last = MTTKRP of the last mode with the given factors.                   */
+double orc_cp_fit(int nmodes, const uint32_t *dims, int64_t nnz, const uint32_t *const *idx, const double *val,
+                  int R, const double *const *factors, const double *lambda)
+{
+    int last = nmodes - 1;
+    double *M = (double *)malloc(sizeof(double) * (size_t)dims[last] * R);
+    double *V = (double *)malloc(sizeof(double) * (size_t)R * R);
+    double *G = (double *)malloc(sizeof(double) * (size_t)R * R);
+    orc_mttkrp(nmodes, dims, nnz, idx, val, factors, R, last, M);
+    double normX2 = 0.0, xhat2 = 0.0, inner = 0.0;
+    for (int64_t p = 0; p < nnz; ++p) normX2 += val[p] * val[p];
+    for (int a = 0; a < R * R; ++a) V[a] = 1.0;
+    for (int k = 0; k < nmodes; ++k) {
+        orc_gram(factors[k], dims[k], R, G);
+        for (int a = 0; a < R * R; ++a) V[a] *= G[a];
+    }
+    for (int a = 0; a < R; ++a)
+        for (int b = 0; b < R; ++b) xhat2 += lambda[a] * V[a * R + b] * lambda[b];
+    for (int r = 0; r < R; ++r) {
+        double s = 0.0;
+        for (uint32_t i = 0; i < dims[last]; ++i) s += M[(size_t)i * R + r] * factors[last][(size_t)i * R + r];
+        inner += lambda[r] * s;
+    }
+    double resid2 = normX2 + xhat2 - 2.0 * inner;
+    free(M);
+    free(V);
+    free(G);
+    return 1.0 - sqrt(resid2 > 0.0 ? resid2 : 0.0) / sqrt(normX2);
+}

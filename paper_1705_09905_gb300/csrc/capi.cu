@@ -1,0 +1,198 @@
+// capi.cu -- status plumbing, allocation hook and the handle queries of the
+// libfcoo C ABI (fcoo_last_error, fcoo_info, fcoo_copy_layout, ...).
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+
+#include "internal.cuh"
+
+namespace fcx {
+
+static thread_local char g_msg[512] = "";
+
+void clear_error() { g_msg[0] = 0; }
+
+int fail(int status, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    int st = (e == cudaErrorMemoryAllocation) ? FCOO_ERR_NOMEM : FCOO_ERR_CUDA;
+    cudaGetLastError();  // clear the sticky-free error state for the next call
+    return fail(st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// FCOO_FAULT_ALLOC=k: the k-th device allocation of the process fails.
+static std::atomic<long> g_alloc_count{0};
+static long fault_at() {
+    static long v = -2;
+    if (v == -2) {
+        const char *s = getenv("FCOO_FAULT_ALLOC");
+        v = (s && *s) ? atol(s) : -1;
+    }
+    return v;
+}
+
+static bool inject_alloc_fault() {
+    long k = fault_at();
+    long n = ++g_alloc_count;
+    return k > 0 && n == k;
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (inject_alloc_fault()) return cudaErrorMemoryAllocation;
+    if (bytes == 0) bytes = 256;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_alloc_async(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (inject_alloc_fault()) return cudaErrorMemoryAllocation;
+    if (bytes == 0) bytes = 256;
+    return cudaMallocAsync(p, bytes, s);
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+void dev_free_async(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+int num_sms() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+void stream_params_from(const fcoo_t *X, StreamParams &p) {
+    memset(&p, 0, sizeof(p));
+    for (int m = 0; m < X->nprod; ++m) p.pidx[m] = X->pidx[m];
+    p.val = X->val;
+    p.bf = X->bf;
+    p.sf = X->sf;
+    p.hcount = X->hcount;
+    p.segrow = X->op == FCOO_OP_MTTKRP ? X->segkeys : nullptr;
+    p.carry_val = X->carry_val;
+    p.carry_seg = X->carry_seg;
+    p.counter = X->counter;
+    p.perm = X->perm;
+    p.nnz = X->nnz;
+    p.nseg = X->nseg;
+    p.nprod = X->nprod;
+    p.threadlen = X->threadlen;
+    p.grid = X->max_grid;
+}
+
+}  // namespace fcx
+
+using namespace fcx;
+
+extern "C" {
+
+const char *fcoo_last_error(void) { return g_msg; }
+
+const char *fcoo_status_string(int status) {
+    switch (status) {
+        case FCOO_OK: return "FCOO_OK";
+        case FCOO_ERR_INVALID_ARG: return "FCOO_ERR_INVALID_ARG";
+        case FCOO_ERR_INDEX_RANGE: return "FCOO_ERR_INDEX_RANGE";
+        case FCOO_ERR_DUPLICATE: return "FCOO_ERR_DUPLICATE";
+        case FCOO_ERR_NOMEM: return "FCOO_ERR_NOMEM";
+        case FCOO_ERR_CUDA: return "FCOO_ERR_CUDA";
+        case FCOO_ERR_NOT_PD: return "FCOO_ERR_NOT_PD";
+        case FCOO_ERR_NONFINITE: return "FCOO_ERR_NONFINITE";
+        case FCOO_ERR_TIMEOUT: return "FCOO_ERR_TIMEOUT";
+        case FCOO_ERR_UNSUPPORTED: return "FCOO_ERR_UNSUPPORTED";
+        default: return "FCOO_ERR_UNKNOWN";
+    }
+}
+
+int fcoo_version(void) { return 10000; }
+
+int64_t fcoo_table2_bytes(int nprod, int64_t nnz, int threadlen) {
+    if (nprod < 1 || nprod >= FCOO_MAX_MODES || nnz < 0 ||
+        threadlen < 1 || threadlen > 64 || (threadlen & (threadlen - 1)) != 0)
+        return -1;
+    int64_t npart = ceil_div(nnz, threadlen);
+    return 4 * nnz + 4 * (int64_t)nprod * nnz + 4 * ceil_div(nnz, 32) + 4 * ceil_div(npart, 32);
+}
+
+int fcoo_destroy(fcoo_t *X) {
+    clear_error();
+    if (!X) return FCOO_OK;
+    cudaDeviceSynchronize();
+    dev_free(X->segkeys);
+    dev_free(X->base);
+    free(X);
+    return FCOO_OK;
+}
+
+int fcoo_info(const fcoo_t *X, fcoo_info_t *info) {
+    clear_error();
+    if (!X || !info) return fail(FCOO_ERR_INVALID_ARG, "fcoo_info: NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->nmodes = X->nmodes;
+    info->mode = X->mode;
+    info->op = X->op;
+    info->threadlen = X->threadlen;
+    info->nnz = X->nnz;
+    info->nseg = X->nseg;
+    info->nfib = X->nfib;
+    for (int k = 0; k < X->nmodes; ++k) info->dims[k] = X->dims[k];
+    info->nprod = X->nprod;
+    info->nidx = X->nidx;
+    for (int k = 0; k < X->nprod; ++k) info->prod_modes[k] = X->prod_modes[k];
+    for (int k = 0; k < X->nidx; ++k) info->idx_modes[k] = X->idx_modes[k];
+    info->bytes_val = X->bytes_val;
+    info->bytes_pidx = X->bytes_pidx;
+    info->bytes_bf = X->bytes_bf;
+    info->bytes_sf = X->bytes_sf;
+    info->bytes_table2 = X->bytes_val + X->bytes_pidx + X->bytes_bf + X->bytes_sf;
+    info->bytes_segmap = X->bytes_segmap;
+    info->bytes_aux = X->bytes_aux;
+    info->bytes_scratch = X->bytes_scratch;
+    return FCOO_OK;
+}
+
+int fcoo_copy_layout(const fcoo_t *X, uint32_t *perm, uint32_t *bf, uint32_t *sf, uint32_t *segkeys,
+                     uint32_t *pidx, float *val, fcoo_stream_t stream) {
+    clear_error();
+    if (!X) return fail(FCOO_ERR_INVALID_ARG, "fcoo_copy_layout: NULL handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t n = (size_t)X->nnz;
+    if (perm && n) FCOO_CUDA(cudaMemcpyAsync(perm, X->perm, n * 4, cudaMemcpyDefault, s));
+    if (bf && n) FCOO_CUDA(cudaMemcpyAsync(bf, X->bf, ceil_div(n, 32) * 4, cudaMemcpyDefault, s));
+    if (sf && n)
+        FCOO_CUDA(cudaMemcpyAsync(sf, X->sf, ceil_div(ceil_div(n, X->threadlen), 32) * 4, cudaMemcpyDefault, s));
+    if (segkeys && X->nseg)
+        FCOO_CUDA(cudaMemcpyAsync(segkeys, X->segkeys, (size_t)X->nseg * X->nidx * 4, cudaMemcpyDefault, s));
+    if (pidx && n)
+        for (int m = 0; m < X->nprod; ++m)
+            FCOO_CUDA(cudaMemcpyAsync(pidx + m * n, X->pidx[m], n * 4, cudaMemcpyDefault, s));
+    if (val && n) FCOO_CUDA(cudaMemcpyAsync(val, X->val, n * 4, cudaMemcpyDefault, s));
+    FCOO_CUDA(cudaStreamSynchronize(s));
+    return FCOO_OK;
+}
+
+int fcoo_fibre_indices(const fcoo_t *X, uint32_t *keys, fcoo_stream_t stream) {
+    clear_error();
+    if (!X || (!keys && X->nseg)) return fail(FCOO_ERR_INVALID_ARG, "fcoo_fibre_indices: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (X->nseg)
+        FCOO_CUDA(cudaMemcpyAsync(keys, X->segkeys, (size_t)X->nseg * X->nidx * 4, cudaMemcpyDefault, s));
+    FCOO_CUDA(cudaStreamSynchronize(s));
+    return FCOO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,736 @@
+// cp_als.cu -- CP-ALS (Algorithm 1) on the device, N-way, one sweep per call.
+//
+// Per mode n (all kernels on the caller's stream, no host round trip):
+//   M   = SpMTTKRP_n(X, F)                         k_stream (spmttkrp.cu)
+//   V   = Hadamard_{k != n} G_k, V^-1 (FP64)         k_solve: Cholesky, or the
+//                                                   eigen pseudo-inverse (cyclic
+//                                                   Jacobi) when a pivot is tiny
+//   Fu  = M * V^-1 (FP32), column sums of squares    k_apply
+//   lambda = column 2-norms (FP64)                   k_lambda
+//   F_n = Fu / lambda, stored as FP32 or BF16         k_normalize (+ <M, F_n> for the fit)
+//   G_n = F_n^T F_n of the stored values (FP64)      k_gram_part + k_gram_reduce
+// after the last mode: fit from the Grams, lambda and <M_last, F_last>   k_fit
+//
+// FP64 is used only for R x R work (Hadamard of Grams, factorisation,
+// inverse, lambda, fit) and for the cross-block sums of the Gram / norm
+// partials; the I x R work is FP32.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+struct cp_state {
+    int nmodes, R, dtype;
+    uint32_t dims[FCOO_MAX_MODES];
+    int64_t max_dim;
+    void *F[FCOO_MAX_MODES];        // factors, dims[k] x R, dtype
+    double *gram[FCOO_MAX_MODES];   // R x R FP64 Grams of the stored factors
+    double *lambda;                 // R
+    float *M;                       // max_dim x R: MTTKRP of the current mode
+    float *Fu;                      // max_dim x R: unnormalised update
+    double *V, *Q, *W;              // R x R FP64 work: normal matrix, eigenvectors, inverse
+    float *Wf;                      // R x R FP32 copy of the inverse for the apply
+    double *part;                   // block partials
+    double *scal;                   // [0] |X|^2, [1] fit, [2] <X, Xhat>, [3] |Xhat|^2
+    int *flags;                     // [0] pseudo-inverse solves, [1] non-finite seen
+    int iters;
+    bool have_norm;
+    void *base;
+    size_t bytes;
+};
+
+namespace fcx {
+namespace {
+
+constexpr int kRowsPerBlock = 128;  // rows per CTA in the I x R kernels
+constexpr int kSolveThreads = 256;
+
+int64_t max_blocks(int64_t max_dim) { return ceil_div(max_dim, kRowsPerBlock); }
+
+template <typename TF>
+__device__ __forceinline__ float ldf(const TF *p);
+template <>
+__device__ __forceinline__ float ldf<float>(const float *p) { return *p; }
+template <>
+__device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+// ---------------------------------------------------------------- |X|^2
+
+__global__ void k_sumsq_part(const float *val, int64_t n, double *part) {
+    double s = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        double v = val[p];
+        s += v * v;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_final(const double *part, int nb, double *out) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) s += part[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+// ---------------------------------------------------------------- solve
+
+struct GramList {
+    const double *g[FCOO_MAX_MODES];
+    int n;
+};
+
+// One CTA.  V = Hadamard of the listed Grams; W = V^-1 via FP64 Cholesky,
+// or, when a pivot d <= 1e-12 * max diag(V), the Moore-Penrose inverse from
+// a cyclic Jacobi eigendecomposition dropping |w| <= 1e-12 * max |w|.
+__global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, double *V, double *Q, double *W,
+                                                         float *Wf, int *flags) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double s_dmax, s_c, s_s;
+    __shared__ int s_ok, s_done;
+    for (int e = tid; e < R * R; e += nt) {
+        double v = 1.0;
+        for (int k = 0; k < gl.n; ++k) v *= gl.g[k][e];
+        V[e] = v;
+        Q[e] = v;  // copy kept for the eigen fallback
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        int finite = 1;
+        for (int i = 0; i < R; ++i) m = fmax(m, V[i * R + i]);
+        for (int e = 0; e < R * R; ++e) finite &= isfinite(V[e]) ? 1 : 0;
+        if (!finite) atomicOr(flags + 1, 1);
+        s_dmax = m;
+        s_ok = (m > 0.0 && finite) ? 1 : 0;
+    }
+    __syncthreads();
+    // right-looking Cholesky in place (lower triangle)
+    for (int j = 0; j < R && s_ok; ++j) {
+        if (tid == 0) {
+            double d = V[j * R + j];
+            if (!(d > 1e-12 * s_dmax)) s_ok = 0;
+            else V[j * R + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const double ljj = V[j * R + j];
+        for (int i = j + 1 + tid; i < R; i += nt) V[i * R + j] /= ljj;
+        __syncthreads();
+        const int m = R - j - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) V[i * R + k] -= V[i * R + j] * V[k * R + j];
+        }
+        __syncthreads();
+    }
+    if (s_ok) {
+        // W = L^-T L^-1: column c of L^-1 by forward substitution (thread c),
+        // kept in the upper triangle of W transposed: W[c*R + i] = Linv[i][c]
+        for (int c = tid; c < R; c += nt) {
+            for (int i = 0; i < R; ++i) {
+                double s = (i == c) ? 1.0 : 0.0;
+                if (i < c) {
+                    W[c * R + i] = 0.0;
+                    continue;
+                }
+                for (int k = c; k < i; ++k) s -= V[i * R + k] * W[c * R + k];
+                W[c * R + i] = s / V[i * R + i];
+            }
+        }
+        __syncthreads();
+        // V <- (L^-1)^T L^-1 ; entry (a,b) = sum_k Linv[k][a] Linv[k][b]
+        for (int e = tid; e < R * R; e += nt) {
+            int a = e / R, b = e % R;
+            int k0 = a > b ? a : b;
+            double s = 0.0;
+            for (int k = k0; k < R; ++k) s += W[a * R + k] * W[b * R + k];
+            V[e] = s;
+        }
+        __syncthreads();
+        for (int e = tid; e < R * R; e += nt) {
+            W[e] = V[e];
+            Wf[e] = (float)V[e];
+        }
+        return;
+    }
+    // ---- pseudo-inverse through the symmetric eigendecomposition
+    if (tid == 0) atomicAdd(flags, 1);
+    // A (in V) <- copy of the normal matrix, Q (eigenvectors) <- I
+    for (int e = tid; e < R * R; e += nt) {
+        V[e] = Q[e];
+        Q[e] = (e / R == e % R) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        if (tid == 0) {
+            double off = 0.0, tot = 0.0;
+            for (int i = 0; i < R; ++i)
+                for (int j = 0; j < R; ++j) {
+                    double a = V[i * R + j];
+                    tot += a * a;
+                    if (i != j) off += a * a;
+                }
+            s_done = (off <= 1e-30 * tot || off == 0.0) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_done) break;
+        for (int p = 0; p < R - 1; ++p)
+            for (int q = p + 1; q < R; ++q) {
+                if (tid == 0) {
+                    double apq = V[p * R + q];
+                    if (apq == 0.0) {
+                        s_c = 1.0;
+                        s_s = 0.0;
+                    } else {
+                        double theta = (V[q * R + q] - V[p * R + p]) / (2.0 * apq);
+                        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        s_c = 1.0 / sqrt(t * t + 1.0);
+                        s_s = t * s_c;
+                    }
+                }
+                __syncthreads();
+                const double c = s_c, s = s_s;
+                if (s != 0.0) {
+                    for (int k = tid; k < R; k += nt) {  // columns p, q
+                        double akp = V[k * R + p], akq = V[k * R + q];
+                        V[k * R + p] = c * akp - s * akq;
+                        V[k * R + q] = s * akp + c * akq;
+                    }
+                    __syncthreads();
+                    for (int k = tid; k < R; k += nt) {  // rows p, q
+                        double apk = V[p * R + k], aqk = V[q * R + k];
+                        V[p * R + k] = c * apk - s * aqk;
+                        V[q * R + k] = s * apk + c * aqk;
+                        double qkp = Q[k * R + p], qkq = Q[k * R + q];
+                        Q[k * R + p] = c * qkp - s * qkq;
+                        Q[k * R + q] = s * qkp + c * qkq;
+                    }
+                }
+                __syncthreads();
+            }
+    }
+    __shared__ double s_wmax;
+    if (tid == 0) {
+        double m = 0.0;
+        for (int i = 0; i < R; ++i) m = fmax(m, fabs(V[i * R + i]));
+        s_wmax = m;
+    }
+    __syncthreads();
+    for (int e = tid; e < R * R; e += nt) {
+        int a = e / R, b = e % R;
+        double s = 0.0;
+        for (int k = 0; k < R; ++k) {
+            double w = V[k * R + k];
+            if (fabs(w) <= 1e-12 * s_wmax || w == 0.0) continue;
+            s += Q[a * R + k] * Q[b * R + k] / w;
+        }
+        W[e] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < R * R; e += nt) Wf[e] = (float)W[e];
+}
+
+// ---------------------------------------------------------------- I x R kernels
+
+// Fu = M * W (FP32), one CTA per kRowsPerBlock rows; column sums of squares
+// of Fu per CTA into part[blk * R + c] (FP64).
+__global__ void k_apply(const float *M, const float *Wf, int64_t I, int R, float *Fu, double *part) {
+    extern __shared__ __align__(16) float sm[];
+    float *sW = sm;            // R x R
+    float *sM = sm + R * R;    // kRowsPerBlock x R
+    const int64_t i0 = (int64_t)blockIdx.x * kRowsPerBlock;
+    const int rows = (int)min((int64_t)kRowsPerBlock, I - i0);
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) sW[e] = Wf[e];
+    for (int e = threadIdx.x; e < rows * R; e += blockDim.x) sM[e] = M[i0 * R + e];
+    __syncthreads();
+    // blockDim.x is a multiple of R: thread (r0, c) handles column c of rows r0, r0 + step, ...
+    const int c = threadIdx.x % R, r0 = threadIdx.x / R, step = blockDim.x / R;
+    __shared__ double red[1024];
+    double sq = 0.0;
+    for (int r = r0; r < rows; r += step) {
+        float s = 0.f;
+        for (int k = 0; k < R; ++k) s = fmaf(sM[r * R + k], sW[k * R + c], s);
+        Fu[(i0 + r) * R + c] = s;
+        sq += (double)s * s;
+    }
+    red[r0 * R + c] = sq;
+    __syncthreads();
+    if (r0 == 0) {
+        double t = 0.0;
+        for (int q = 0; q < step; ++q) t += red[q * R + c];
+        part[(int64_t)blockIdx.x * R + c] = t;
+    }
+}
+
+// lambda_c = sqrt(sum_b part[b][c]); one CTA.
+__global__ void k_lambda(const double *part, int nb, int R, double *lambda, int *flags) {
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[(int64_t)b * R + c];
+        double l = sqrt(s);
+        if (!isfinite(l)) atomicOr(flags + 1, 1);
+        lambda[c] = l;
+    }
+}
+
+// F = Fu / lambda (columns with lambda = 0 kept as they are), stored as TF;
+// optional per-CTA partial of sum_i M(i,c) * F(i,c) with the stored F.
+template <typename TF>
+__global__ void k_normalize(const float *Fu, const double *lambda, int64_t I, int R, TF *F, const float *M,
+                            double *dotpart) {
+    const int64_t i0 = (int64_t)blockIdx.x * kRowsPerBlock;
+    const int rows = (int)min((int64_t)kRowsPerBlock, I - i0);
+    __shared__ double red[1024];
+    const int c = threadIdx.x % R, r0 = threadIdx.x / R, step = blockDim.x / R;
+    const double l = lambda[c];
+    const float inv = l > 0.0 ? (float)(1.0 / l) : 1.0f;
+    double dot = 0.0;
+    for (int r = r0; r < rows; r += step) {
+        const int64_t e = (i0 + r) * R + c;
+        float v = Fu[e] * inv;
+        TF st;
+        if constexpr (sizeof(TF) == 2) st = __float2bfloat16_rn(v);
+        else st = v;
+        F[e] = st;
+        if (dotpart) dot += (double)M[e] * (double)ldf<TF>(&st);
+    }
+    if (dotpart) {
+        red[r0 * R + c] = dot;
+        __syncthreads();
+        if (r0 == 0) {
+            double t = 0.0;
+            for (int q = 0; q < step; ++q) t += red[q * R + c];
+            dotpart[(int64_t)blockIdx.x * R + c] = t;
+        }
+    }
+}
+
+// Per-CTA Gram partial of the stored factor rows [i0, i0 + rows): FP32 sums
+// of kRowsPerBlock products, written as FP64.
+template <typename TF>
+__global__ void k_gram_part(const TF *F, int64_t I, int R, double *part) {
+    extern __shared__ __align__(16) float sF[];
+    const int64_t i0 = (int64_t)blockIdx.x * kRowsPerBlock;
+    const int rows = (int)min((int64_t)kRowsPerBlock, I - i0);
+    for (int e = threadIdx.x; e < rows * R; e += blockDim.x) sF[e] = ldf<TF>(F + i0 * R + e);
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const int a = e / R, b = e % R;
+        float s = 0.f;
+        for (int r = 0; r < rows; ++r) s = fmaf(sF[r * R + a], sF[r * R + b], s);
+        part[(int64_t)blockIdx.x * R * R + e] = s;
+    }
+}
+
+__global__ void k_gram_reduce(const double *part, int nb, int R, double *G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= R * R) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * R * R + e];
+    G[e] = s;
+}
+
+struct GramAll {
+    const double *g[FCOO_MAX_MODES];
+    int n;
+};
+
+// fit = 1 - sqrt(max(0, |X|^2 + |Xhat|^2 - 2 <X,Xhat>)) / |X| ; one CTA.
+__global__ void k_fit(GramAll ga, const double *lambda, int R, const double *dotpart, int nb, double *scal) {
+    __shared__ double red[256];
+    double xh = 0.0, inner = 0.0;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        double v = lambda[e / R] * lambda[e % R];
+        for (int k = 0; k < ga.n; ++k) v *= ga.g[k][e];
+        xh += v;
+    }
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += dotpart[(int64_t)b * R + c];
+        inner += lambda[c] * s;
+    }
+    red[threadIdx.x] = xh;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double xhat2 = red[0];
+    __syncthreads();
+    red[threadIdx.x] = inner;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double in = red[0], nx = scal[0];
+        const double r2 = nx + xhat2 - 2.0 * in;
+        scal[1] = 1.0 - sqrt(r2 > 0.0 ? r2 : 0.0) / sqrt(nx);
+        scal[2] = in;
+        scal[3] = xhat2;
+    }
+}
+
+__global__ void k_to_dtype(const float *src, int64_t n, __nv_bfloat16 *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+__global__ void k_to_f32(const __nv_bfloat16 *src, int64_t n, float *dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __bfloat162float(src[i]);
+}
+
+unsigned gs(int64_t n) {
+    int64_t b = ceil_div(n, 256);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 4096));
+}
+
+int gram_of(cp_state_t *st, int k, cudaStream_t s) {
+    const int R = st->R;
+    const int64_t I = st->dims[k];
+    const int nb = (int)ceil_div(I, kRowsPerBlock);
+    const size_t smem = (size_t)kRowsPerBlock * R * 4;
+    if (st->dtype == FCOO_BF16) {
+        FCOO_CUDA(cudaFuncSetAttribute(k_gram_part<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+        k_gram_part<__nv_bfloat16><<<nb, 256, smem, s>>>((const __nv_bfloat16 *)st->F[k], I, R, st->part);
+    } else {
+        FCOO_CUDA(cudaFuncSetAttribute(k_gram_part<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_gram_part<float><<<nb, 256, smem, s>>>((const float *)st->F[k], I, R, st->part);
+    }
+    FCOO_CUDA(cudaGetLastError());
+    k_gram_reduce<<<(unsigned)ceil_div(R * R, 256), 256, 0, s>>>(st->part, nb, R, st->gram[k]);
+    FCOO_CUDA(cudaGetLastError());
+    return FCOO_OK;
+}
+
+// One mode update of Algorithm 1.
+int mode_update(const fcoo_t *X, cp_state_t *st, int n, bool last, cudaStream_t s) {
+    const int R = st->R;
+    const int64_t I = st->dims[n];
+    // M = SpMTTKRP_n
+    StreamParams p;
+    stream_params_from(X, p);
+    for (int m = 0; m < X->nprod; ++m) p.F[m] = st->F[X->prod_modes[m]];
+    p.out = st->M;
+    p.R = R;
+    p.out_rows = I;
+    if (X->nnz == 0) {
+        FCOO_CUDA(cudaMemsetAsync(st->M, 0, (size_t)I * R * 4, s));
+    } else {
+        int rc = launch_stream_kernel(p, st->dtype, s);
+        if (rc) return rc;
+    }
+    // V, V^-1
+    GramList gl;
+    memset(&gl, 0, sizeof(gl));
+    for (int k = 0; k < st->nmodes; ++k)
+        if (k != n) gl.g[gl.n++] = st->gram[k];
+    k_solve<<<1, kSolveThreads, 0, s>>>(gl, R, st->V, st->Q, st->W, st->Wf, st->flags);
+    FCOO_CUDA(cudaGetLastError());
+    // Fu = M W, column norms
+    const int nb = (int)ceil_div(I, kRowsPerBlock);
+    const int threads = R >= 256 ? R : (256 / R) * R;  // a multiple of R
+    const size_t smem = ((size_t)R * R + (size_t)kRowsPerBlock * R) * 4;
+    FCOO_CUDA(cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_apply<<<nb, threads, smem, s>>>(st->M, st->Wf, I, R, st->Fu, st->part);
+    FCOO_CUDA(cudaGetLastError());
+    k_lambda<<<1, 256, 0, s>>>(st->part, nb, R, st->lambda, st->flags);
+    FCOO_CUDA(cudaGetLastError());
+    double *dotpart = last ? st->part : nullptr;
+    if (st->dtype == FCOO_BF16)
+        k_normalize<__nv_bfloat16><<<nb, threads, 0, s>>>(st->Fu, st->lambda, I, R, (__nv_bfloat16 *)st->F[n],
+                                                          st->M, dotpart);
+    else
+        k_normalize<float><<<nb, threads, 0, s>>>(st->Fu, st->lambda, I, R, (float *)st->F[n], st->M, dotpart);
+    FCOO_CUDA(cudaGetLastError());
+    return FCOO_OK;
+}
+
+}  // namespace
+}  // namespace fcx
+
+using namespace fcx;
+
+extern "C" int cp_state_create(int nmodes, const uint32_t *dims, int R, int dtype, const float *const *init,
+                               fcoo_stream_t stream, cp_state_t **out) {
+    clear_error();
+    if (!out) return fail(FCOO_ERR_INVALID_ARG, "cp_state_create: out is NULL");
+    *out = nullptr;
+    if (nmodes < 2 || nmodes > FCOO_MAX_MODES || !dims || !init)
+        return fail(FCOO_ERR_INVALID_ARG, "cp_state_create: bad nmodes/dims/init");
+    if (R < 1 || R > 128) return fail(FCOO_ERR_INVALID_ARG, "cp_state_create: R=%d outside 1..128", R);
+    if (dtype != FCOO_F32 && dtype != FCOO_BF16) return fail(FCOO_ERR_INVALID_ARG, "cp_state_create: bad dtype");
+    for (int k = 0; k < nmodes; ++k) {
+        if (dims[k] == 0) return fail(FCOO_ERR_INVALID_ARG, "cp_state_create: dims[%d] is 0", k);
+        if (!init[k]) return fail(FCOO_ERR_INVALID_ARG, "cp_state_create: init[%d] is NULL", k);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cp_state_t *st = (cp_state_t *)calloc(1, sizeof(cp_state_t));
+    if (!st) return fail(FCOO_ERR_NOMEM, "cp_state_create: host allocation failed");
+    st->nmodes = nmodes;
+    st->R = R;
+    st->dtype = dtype;
+    st->max_dim = 0;
+    for (int k = 0; k < nmodes; ++k) {
+        st->dims[k] = dims[k];
+        st->max_dim = std::max<int64_t>(st->max_dim, dims[k]);
+    }
+    const size_t es = dtype == FCOO_BF16 ? 2 : 4;
+    const int64_t nbmax = max_blocks(st->max_dim);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off += round_up((int64_t)b, 256);
+        return o;
+    };
+    size_t oF[FCOO_MAX_MODES], oG[FCOO_MAX_MODES];
+    for (int k = 0; k < nmodes; ++k) oF[k] = take((size_t)dims[k] * R * es);
+    for (int k = 0; k < nmodes; ++k) oG[k] = take((size_t)R * R * 8);
+    size_t oL = take(R * 8), oM = take((size_t)st->max_dim * R * 4), oFu = take((size_t)st->max_dim * R * 4);
+    size_t oV = take((size_t)R * R * 8), oQ = take((size_t)R * R * 8), oW = take((size_t)R * R * 8);
+    size_t oWf = take((size_t)R * R * 4);
+    size_t oP = take((size_t)std::max<int64_t>(nbmax * R * R, 4096) * 8);
+    size_t oS = take(8 * 8), oFl = take(16);
+    cudaError_t e = dev_alloc(&st->base, off);
+    if (e != cudaSuccess) {
+        free(st);
+        return cuda_fail(e, "cp_state_create: cudaMalloc");
+    }
+    st->bytes = off;
+    char *b = (char *)st->base;
+    for (int k = 0; k < nmodes; ++k) {
+        st->F[k] = b + oF[k];
+        st->gram[k] = (double *)(b + oG[k]);
+    }
+    st->lambda = (double *)(b + oL);
+    st->M = (float *)(b + oM);
+    st->Fu = (float *)(b + oFu);
+    st->V = (double *)(b + oV);
+    st->Q = (double *)(b + oQ);
+    st->W = (double *)(b + oW);
+    st->Wf = (float *)(b + oWf);
+    st->part = (double *)(b + oP);
+    st->scal = (double *)(b + oS);
+    st->flags = (int *)(b + oFl);
+    int rc = FCOO_OK;
+    auto cu = [&](cudaError_t ce, const char *what) {
+        if (ce != cudaSuccess && rc == FCOO_OK) rc = cuda_fail(ce, what);
+    };
+    cu(cudaMemsetAsync(st->base, 0, off, s), "cudaMemsetAsync");
+    for (int k = 0; k < nmodes && rc == FCOO_OK; ++k) {
+        const size_t n = (size_t)dims[k] * R;
+        if (dtype == FCOO_F32) {
+            cu(cudaMemcpyAsync(st->F[k], init[k], n * 4, cudaMemcpyDefault, s), "cudaMemcpyAsync(init)");
+        } else {
+            cu(cudaMemcpyAsync(st->Fu, init[k], n * 4, cudaMemcpyDefault, s), "cudaMemcpyAsync(init)");
+            k_to_dtype<<<gs(n), 256, 0, s>>>(st->Fu, n, (__nv_bfloat16 *)st->F[k]);
+            cu(cudaGetLastError(), "k_to_dtype");
+        }
+        if (rc == FCOO_OK) rc = gram_of(st, k, s);
+    }
+    {
+        double ones[FCOO_MAX_RANK];
+        for (int r = 0; r < R; ++r) ones[r] = 1.0;
+        cu(cudaMemcpyAsync(st->lambda, ones, R * 8, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(lambda)");
+        cu(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    }
+    if (rc != FCOO_OK) {
+        dev_free(st->base);
+        free(st);
+        return rc;
+    }
+    *out = st;
+    return FCOO_OK;
+}
+
+extern "C" int cp_state_destroy(cp_state_t *st) {
+    clear_error();
+    if (!st) return FCOO_OK;
+    cudaDeviceSynchronize();
+    dev_free(st->base);
+    free(st);
+    return FCOO_OK;
+}
+
+extern "C" int cp_als_iter(const fcoo_t *const *Xn, cp_state_t *st, fcoo_stream_t stream) {
+    clear_error();
+    if (!Xn || !st) return fail(FCOO_ERR_INVALID_ARG, "cp_als_iter: NULL argument");
+    for (int n = 0; n < st->nmodes; ++n) {
+        const fcoo_t *X = Xn[n];
+        if (!X) return fail(FCOO_ERR_INVALID_ARG, "cp_als_iter: Xn[%d] is NULL", n);
+        if (X->op != FCOO_OP_MTTKRP || X->mode != n || X->nmodes != st->nmodes)
+            return fail(FCOO_ERR_INVALID_ARG, "cp_als_iter: Xn[%d] is not an SpMTTKRP handle for mode %d", n, n);
+        for (int k = 0; k < st->nmodes; ++k)
+            if (X->dims[k] != st->dims[k]) return fail(FCOO_ERR_INVALID_ARG, "cp_als_iter: Xn[%d] dims differ", n);
+        if (X->nnz != Xn[0]->nnz) return fail(FCOO_ERR_INVALID_ARG, "cp_als_iter: handles hold different tensors");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int R = st->R;
+    if (!st->have_norm) {
+        const fcoo_t *X = Xn[0];
+        const int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, ceil_div(X->nnz, 256)));
+        k_sumsq_part<<<nb, 256, 0, s>>>(X->val, X->nnz, st->part);
+        k_sum_final<<<1, 256, 0, s>>>(st->part, nb, st->scal);
+        FCOO_CUDA(cudaGetLastError());
+        st->have_norm = true;
+    }
+    for (int n = 0; n < st->nmodes; ++n) {
+        const bool last = n == st->nmodes - 1;
+        int rc = mode_update(Xn[n], st, n, last, s);
+        if (rc) return rc;
+        const int nb = (int)ceil_div(st->dims[n], kRowsPerBlock);
+        if (last) {
+            // move the <M, F_last> partials out of `part` before the Gram pass reuses it
+            FCOO_CUDA(cudaMemcpyAsync(st->Fu, st->part, (size_t)nb * R * 8, cudaMemcpyDeviceToDevice, s));
+        }
+        rc = gram_of(st, n, s);
+        if (rc) return rc;
+        if (last) {
+            GramAll ga;
+            memset(&ga, 0, sizeof(ga));
+            for (int k = 0; k < st->nmodes; ++k) ga.g[ga.n++] = st->gram[k];
+            k_fit<<<1, 256, 0, s>>>(ga, st->lambda, R, (const double *)st->Fu, nb, st->scal);
+            FCOO_CUDA(cudaGetLastError());
+        }
+    }
+    st->iters++;
+    return FCOO_OK;
+}
+
+extern "C" int cp_state_stats(const cp_state_t *st, double *lambda, double *fit, int *iters, int *npinv,
+                              fcoo_stream_t stream) {
+    clear_error();
+    if (!st) return fail(FCOO_ERR_INVALID_ARG, "cp_state_stats: NULL state");
+    cudaStream_t s = (cudaStream_t)stream;
+    double scal[4];
+    int flags[2];
+    FCOO_CUDA(cudaMemcpyAsync(scal, st->scal, sizeof(scal), cudaMemcpyDeviceToHost, s));
+    FCOO_CUDA(cudaMemcpyAsync(flags, st->flags, sizeof(flags), cudaMemcpyDeviceToHost, s));
+    if (lambda) FCOO_CUDA(cudaMemcpyAsync(lambda, st->lambda, st->R * 8, cudaMemcpyDeviceToHost, s));
+    FCOO_CUDA(cudaStreamSynchronize(s));
+    if (fit) *fit = scal[1];
+    if (iters) *iters = st->iters;
+    if (npinv) *npinv = flags[0];
+    if (flags[1]) return fail(FCOO_ERR_NONFINITE, "cp_state_stats: a non-finite value appeared in the normal equations");
+    return FCOO_OK;
+}
+
+extern "C" int cp_state_copy_factor(const cp_state_t *st, int k, float *dst, fcoo_stream_t stream) {
+    clear_error();
+    if (!st || !dst || k < 0 || k >= st->nmodes) return fail(FCOO_ERR_INVALID_ARG, "cp_state_copy_factor: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)st->dims[k] * st->R;
+    if (st->dtype == FCOO_F32) {
+        FCOO_CUDA(cudaMemcpyAsync(dst, st->F[k], n * 4, cudaMemcpyDefault, s));
+    } else {
+        k_to_f32<<<gs(n), 256, 0, s>>>((const __nv_bfloat16 *)st->F[k], n, st->Fu);
+        FCOO_CUDA(cudaGetLastError());
+        FCOO_CUDA(cudaMemcpyAsync(dst, st->Fu, n * 4, cudaMemcpyDefault, s));
+    }
+    FCOO_CUDA(cudaStreamSynchronize(s));
+    return FCOO_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+
+namespace {
+struct BlobHeader {
+    uint64_t magic;
+    int32_t nmodes, R, dtype, iters;
+    uint32_t dims[FCOO_MAX_MODES];
+    int32_t have_norm, pad;
+};
+constexpr uint64_t kMagic = 0x31504f4f43464350ull;  // "PCFCOOP1"
+
+int64_t blob_bytes(const cp_state_t *st) {
+    const size_t es = st->dtype == FCOO_BF16 ? 2 : 4;
+    int64_t b = sizeof(BlobHeader);
+    for (int k = 0; k < st->nmodes; ++k) b += (int64_t)st->dims[k] * st->R * es + (int64_t)st->R * st->R * 8;
+    b += (int64_t)st->R * 8 + 4 * 8 + 2 * 4;
+    return b;
+}
+}  // namespace
+
+extern "C" int64_t cp_state_blob_size(const cp_state_t *st) { return st ? blob_bytes(st) : -1; }
+
+extern "C" int cp_state_save(const cp_state_t *st, void *blob, int64_t size, fcoo_stream_t stream) {
+    clear_error();
+    if (!st || !blob || size < blob_bytes(st)) return fail(FCOO_ERR_INVALID_ARG, "cp_state_save: bad argument or size");
+    cudaStream_t s = (cudaStream_t)stream;
+    BlobHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = kMagic;
+    h.nmodes = st->nmodes;
+    h.R = st->R;
+    h.dtype = st->dtype;
+    h.iters = st->iters;
+    h.have_norm = st->have_norm;
+    for (int k = 0; k < st->nmodes; ++k) h.dims[k] = st->dims[k];
+    char *p = (char *)blob;
+    memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const size_t es = st->dtype == FCOO_BF16 ? 2 : 4;
+    for (int k = 0; k < st->nmodes; ++k) {
+        const size_t n = (size_t)st->dims[k] * st->R * es;
+        FCOO_CUDA(cudaMemcpyAsync(p, st->F[k], n, cudaMemcpyDeviceToHost, s));
+        p += n;
+        FCOO_CUDA(cudaMemcpyAsync(p, st->gram[k], (size_t)st->R * st->R * 8, cudaMemcpyDeviceToHost, s));
+        p += (size_t)st->R * st->R * 8;
+    }
+    FCOO_CUDA(cudaMemcpyAsync(p, st->lambda, (size_t)st->R * 8, cudaMemcpyDeviceToHost, s));
+    p += (size_t)st->R * 8;
+    FCOO_CUDA(cudaMemcpyAsync(p, st->scal, 4 * 8, cudaMemcpyDeviceToHost, s));
+    p += 4 * 8;
+    FCOO_CUDA(cudaMemcpyAsync(p, st->flags, 2 * 4, cudaMemcpyDeviceToHost, s));
+    FCOO_CUDA(cudaStreamSynchronize(s));
+    return FCOO_OK;
+}
+
+extern "C" int cp_state_load(cp_state_t *st, const void *blob, int64_t size, fcoo_stream_t stream) {
+    clear_error();
+    if (!st || !blob || size < (int64_t)sizeof(BlobHeader)) return fail(FCOO_ERR_INVALID_ARG, "cp_state_load: bad argument");
+    BlobHeader h;
+    memcpy(&h, blob, sizeof(h));
+    if (h.magic != kMagic || h.nmodes != st->nmodes || h.R != st->R || h.dtype != st->dtype)
+        return fail(FCOO_ERR_INVALID_ARG, "cp_state_load: blob does not match this state");
+    for (int k = 0; k < st->nmodes; ++k)
+        if (h.dims[k] != st->dims[k]) return fail(FCOO_ERR_INVALID_ARG, "cp_state_load: dims differ");
+    if (size < blob_bytes(st)) return fail(FCOO_ERR_INVALID_ARG, "cp_state_load: blob too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    const char *p = (const char *)blob + sizeof(h);
+    const size_t es = st->dtype == FCOO_BF16 ? 2 : 4;
+    for (int k = 0; k < st->nmodes; ++k) {
+        const size_t n = (size_t)st->dims[k] * st->R * es;
+        FCOO_CUDA(cudaMemcpyAsync(st->F[k], p, n, cudaMemcpyHostToDevice, s));
+        p += n;
+        FCOO_CUDA(cudaMemcpyAsync(st->gram[k], p, (size_t)st->R * st->R * 8, cudaMemcpyHostToDevice, s));
+        p += (size_t)st->R * st->R * 8;
+    }
+    FCOO_CUDA(cudaMemcpyAsync(st->lambda, p, (size_t)st->R * 8, cudaMemcpyHostToDevice, s));
+    p += (size_t)st->R * 8;
+    FCOO_CUDA(cudaMemcpyAsync(st->scal, p, 4 * 8, cudaMemcpyHostToDevice, s));
+    p += 4 * 8;
+    FCOO_CUDA(cudaMemcpyAsync(st->flags, p, 2 * 4, cudaMemcpyHostToDevice, s));
+    FCOO_CUDA(cudaStreamSynchronize(s));
+    st->iters = h.iters;
+    st->have_norm = h.have_norm != 0;
+    return FCOO_OK;
+}

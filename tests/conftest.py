@@ -10,6 +10,12 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built libfcoo.so")
+    # the C ABI tests load libfcoo.so: build it (nvcc cross-compiles without a GPU)
+    lib = os.path.join(ROOT, "paper_1705_09905_gb300", "lib", "libfcoo.so")
+    if not os.path.exists(lib):
+        import __graft_entry__
+
+        __graft_entry__.build()
 
 
 @pytest.fixture(scope="session")

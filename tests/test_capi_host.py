@@ -1,0 +1,88 @@
+"""Host-only checks of the C ABI: the library loads without a GPU, exports
+every entry point declared in include/fcoo.h, and rejects bad arguments
+before touching the device."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import paper_1705_09905_gb300 as fc
+
+    return fc
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fcoo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][A-Za-z0-9_ \*]*?\b([a-z_][a-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+def test_every_declared_symbol_is_exported(fc):
+    names = declared_functions()
+    assert "spmttkrp" in names and "fcoo_build" in names and len(names) >= 20, names
+    missing = [n for n in names if not hasattr(fc.lib, n)]
+    assert not missing, f"declared in include/fcoo.h but not exported: {missing}"
+
+
+def test_table2_bytes_golden(fc):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "table2_storage.json")))
+    for row in g["rows"]:
+        assert fc.table2_bytes(1, row["nnz"], row["threadlen"]) == row["fcoo_ttm"]
+        assert fc.table2_bytes(2, row["nnz"], row["threadlen"]) == row["fcoo_mttkrp"]
+        assert row["fcoo_mttkrp"] < row["coo"]
+    assert fc.table2_bytes(2, 1000, 7) == -1
+    assert fc.table2_bytes(2, 1000, 128) == -1
+    assert fc.table2_bytes(0, 1000, 8) == -1
+
+
+def test_status_strings(fc):
+    assert fc.lib.fcoo_status_string(0) == b"FCOO_OK"
+    assert fc.lib.fcoo_status_string(-3) == b"FCOO_ERR_DUPLICATE"
+    assert fc.lib.fcoo_version() >= 10000
+
+
+@pytest.mark.parametrize("case", ["nmodes", "dims0", "mode", "op", "threadlen", "nullidx", "nnz"])
+def test_build_rejects_bad_arguments_without_device_work(fc, case):
+    lib = fc.lib
+    dims = (ctypes.c_uint32 * 3)(4, 5, 6)
+    a = (ctypes.c_uint32 * 2)(0, 1)
+    v = (ctypes.c_float * 2)(1.0, 2.0)
+    idx = (ctypes.c_void_p * 3)(ctypes.addressof(a), ctypes.addressof(a), ctypes.addressof(a))
+    args = dict(nmodes=3, dims=ctypes.addressof(dims), nnz=2, idx=idx, val=ctypes.addressof(v), mode=0, op=0,
+                threadlen=8)
+    if case == "nmodes":
+        args["nmodes"] = 1
+    elif case == "dims0":
+        dims[1] = 0
+    elif case == "mode":
+        args["mode"] = 3
+    elif case == "op":
+        args["op"] = 7
+    elif case == "threadlen":
+        args["threadlen"] = 12
+    elif case == "nullidx":
+        idx[2] = None
+    elif case == "nnz":
+        args["nnz"] = -5
+    out = ctypes.c_void_p(1234)
+    st = lib.fcoo_build(args["nmodes"], args["dims"], args["nnz"], ctypes.cast(idx, ctypes.POINTER(ctypes.c_void_p)),
+                        args["val"], args["mode"], args["op"], args["threadlen"], None, ctypes.byref(out))
+    assert st == -1, (case, st)
+    assert out.value is None
+    assert lib.fcoo_last_error().startswith(b"fcoo_build:")
+
+
+def test_compute_entry_points_reject_null_handles(fc):
+    lib = fc.lib
+    assert lib.spmttkrp(None, None, 0, 16, None, None) == -1
+    assert lib.spttm(None, None, 0, 16, None, None) == -1
+    assert b"NULL" in lib.fcoo_last_error()
+    assert lib.fcoo_destroy(None) == 0

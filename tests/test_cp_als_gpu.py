@@ -1,0 +1,128 @@
+"""CP-ALS (Algorithm 1) on the device vs the FP64 oracle: factors, lambda and
+fit per sweep (FP32), the BF16 path against the oracle fed the same rounded
+factors step by step, the pseudo-inverse fallback, monotone fit, exact
+recovery of a low-rank tensor, checkpoint / resume."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import cuda, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import paper_1705_09905_gb300 as fc
+
+    return fc
+
+
+def handles(fc, T, tl=8):
+    return [fc.FCOO.build(T.idx_u32(), T.val.numpy(), T.dims, n, "mttkrp", tl) for n in range(T.nmodes)]
+
+
+def test_fp32_sweeps_match_oracle(fc, oracle):
+    cfg = synth.CONFIGS["tiny"]
+    T = synth.make_tensor(cfg)
+    Xs = handles(fc, T)
+    R = 8
+    init = synth.make_factors(T.dims, R, seed=3, kind="uniform")
+    st = fc.CPState(T.dims, R, init)
+    idx, val = T.idx_u32(), T.val.double().numpy()
+    F = [f.double().numpy() for f in init]
+    fits = []
+    for sweep in range(4):
+        st.iterate(Xs)
+        s = st.stats()
+        for n in range(3):
+            F, lam, _, _ = oracle.cp_als_mode(T.dims, idx, val, F, n)
+        ref_fit = oracle.cp_fit(T.dims, idx, val, F, lam)
+        assert abs(s["fit"] - ref_fit) <= 1e-5, (sweep, s["fit"], ref_fit)
+        assert rel_fro(s["lambda"], lam) <= 1e-4
+        for k in range(3):
+            assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 1e-4, (sweep, k)
+        fits.append(s["fit"])
+        assert s["iters"] == sweep + 1
+    assert all(b >= a - 1e-6 for a, b in zip(fits, fits[1:])), fits
+
+
+def test_bf16_sweep_matches_oracle_with_same_rounding(fc, oracle):
+    cfg = synth.CONFIGS["tiny"]
+    T = synth.make_tensor(cfg)
+    Xs = handles(fc, T)
+    R = 16
+    init = synth.make_factors(T.dims, R, seed=4, kind="uniform")
+    st = fc.CPState(T.dims, R, init, dtype=torch.bfloat16)
+    idx, val = T.idx_u32(), T.val.double().numpy()
+    rnd = lambda a: torch.as_tensor(a).to(torch.bfloat16).double().numpy()  # round to nearest even
+    F = [rnd(f.numpy()) for f in init]
+    for sweep in range(2):
+        st.iterate(Xs)
+        for n in range(3):
+            F, lam, _, _ = oracle.cp_als_mode(T.dims, idx, val, F, n)
+            F[n] = rnd(F[n])
+        s = st.stats()
+        ref_fit = oracle.cp_fit(T.dims, idx, val, F, lam)
+        assert abs(s["fit"] - ref_fit) <= 1e-4, (sweep, s["fit"], ref_fit)
+        for k in range(3):
+            # a few entries may round to the neighbouring bf16 value (FP32 vs FP64 near a tie)
+            assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 2e-3, (sweep, k)
+
+
+def test_pseudo_inverse_fallback(fc, oracle):
+    # modes 1 and 2 of size 1: the mode-0 normal matrix G1 * G2 has rank 1 < R
+    T = synth.random_small((50, 1, 1), 30, seed=5)
+    Xs = handles(fc, T)
+    R = 3
+    init = synth.make_factors(T.dims, R, seed=6, kind="uniform")
+    st = fc.CPState(T.dims, R, init)
+    st.iterate(Xs)
+    s = st.stats()
+    F, lam, fits, npinv = oracle.cp_als(T.dims, T.idx_u32(), T.val.double().numpy(),
+                                        [f.double().numpy() for f in init], 1)
+    assert s["npinv"] == npinv > 0
+    assert abs(s["fit"] - fits[0]) <= 1e-5
+    for k in range(3):
+        assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 1e-4
+
+
+def test_low_rank_recovery_4way(fc):
+    rng = np.random.default_rng(7)
+    dims = (12, 10, 9, 8)
+    A = [rng.standard_normal((d, 2)) for d in dims]
+    X = np.einsum("ir,jr,kr,lr->ijkl", *A)
+    idx = [a.ravel().astype(np.uint32) for a in np.indices(dims)]
+    T = synth.SparseTensor(dims, [torch.as_tensor(a.astype(np.int64)) for a in idx],
+                           torch.as_tensor(X.ravel().astype(np.float32)))
+    Xs = handles(fc, T)
+    st = fc.CPState(dims, 2, synth.make_factors(dims, 2, seed=8, kind="uniform"))
+    st.iterate(Xs, sweeps=60)
+    assert st.fit > 1 - 1e-4
+
+
+def test_checkpoint_resume_is_bitwise(fc):
+    T = synth.make_tensor(synth.scaled(synth.CONFIGS["skewed3"], 100_000, dims=(500, 400, 600)))
+    Xs = handles(fc, T)
+    init = synth.make_factors(T.dims, 16, seed=9, kind="uniform")
+    a = fc.CPState(T.dims, 16, init)
+    a.iterate(Xs, sweeps=2)
+    blob = a.save()
+    a.iterate(Xs, sweeps=2)
+    b = fc.CPState(T.dims, 16, init).load(blob)
+    assert b.stats()["iters"] == 2
+    b.iterate(Xs, sweeps=2)
+    sa, sb = a.stats(), b.stats()
+    assert sa["fit"] == sb["fit"] and sb["iters"] == 4
+    for k in range(3):
+        assert torch.equal(a.factor(k), b.factor(k))
+
+
+def test_argument_errors(fc):
+    T = synth.random_small((20, 30, 40), 500, seed=1)
+    Xs = handles(fc, T)
+    with pytest.raises(fc.FcooError):
+        fc.CPState((20, 30, 41), 4, synth.make_factors((20, 30, 41), 4, seed=1)).iterate(Xs)
+    with pytest.raises(fc.FcooError):
+        fc.CPState(T.dims, 4, synth.make_factors(T.dims, 4, seed=1)).iterate([Xs[1], Xs[0], Xs[2]])

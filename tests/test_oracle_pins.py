@@ -405,3 +405,23 @@ def test_mttkrp_adjoint_identity(oracle):
         Fk = [f.copy() for f in F]
         Fk[k] = D
         np.testing.assert_allclose(np.sum(brute_mttkrp(Xv, Fk, n) * G), np.sum(D * dF[k]), rtol=1e-11)
+
+
+def test_cp_als_mode_steps_compose_to_a_sweep_and_fit_matches_dense(oracle):
+    rng = np.random.default_rng(16)
+    dims = (7, 6, 5)
+    idx, val = rand_coo(rng, dims, 90)
+    init = [rng.uniform(0, 1, (d, 3)) for d in dims]
+    F_ref, lam_ref, fits, _ = oracle.cp_als(dims, idx, val, init, 2)
+    F = [f.copy() for f in init]
+    for _ in range(2):
+        for n in range(3):
+            F, lam, M, _ = oracle.cp_als_mode(dims, idx, val, F, n)
+    for a, b in zip(F, F_ref):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(lam, lam_ref, rtol=1e-12)
+    fit = oracle.cp_fit(dims, idx, val, F, lam)
+    np.testing.assert_allclose(fit, fits[-1], rtol=1e-12)
+    X = densify(dims, idx, val)
+    direct = 1.0 - np.linalg.norm(X - dense_kruskal(lam, F)) / np.linalg.norm(X)
+    np.testing.assert_allclose(fit, direct, rtol=1e-10)
