@@ -46,6 +46,12 @@ namespace {
 
 constexpr int kRowsPerBlock = 128;  // rows per CTA in the I x R kernels
 constexpr int kSolveThreads = 256;
+// Relative size below which a Cholesky pivot or an eigenvalue of V counts as
+// zero.  The Grams are FP64 sums of FP32 partials of FP32/BF16-stored
+// factors, accurate to ~1e-7 relative; a smaller threshold would let rounding
+// noise pass for rank.  (The FP64 oracle, whose Grams are exact to 1e-16,
+// uses 1e-12.)
+constexpr double kRankTol = 1e-6;
 
 int64_t max_blocks(int64_t max_dim) { return ceil_div(max_dim, kRowsPerBlock); }
 
@@ -95,8 +101,8 @@ struct GramList {
 };
 
 // One CTA.  V = Hadamard of the listed Grams; W = V^-1 via FP64 Cholesky,
-// or, when a pivot d <= 1e-12 * max diag(V), the Moore-Penrose inverse from
-// a cyclic Jacobi eigendecomposition dropping |w| <= 1e-12 * max |w|.
+// or, when a pivot d <= kRankTol * max diag(V), the Moore-Penrose inverse from
+// a cyclic Jacobi eigendecomposition dropping |w| <= kRankTol * max |w|.
 __global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, double *V, double *Q, double *W,
                                                          float *Wf, int *flags) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -123,7 +129,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, dou
     for (int j = 0; j < R && s_ok; ++j) {
         if (tid == 0) {
             double d = V[j * R + j];
-            if (!(d > 1e-12 * s_dmax)) s_ok = 0;
+            if (!(d > kRankTol * s_dmax)) s_ok = 0;
             else V[j * R + j] = sqrt(d);
         }
         __syncthreads();
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, dou
         double s = 0.0;
         for (int k = 0; k < R; ++k) {
             double w = V[k * R + k];
-            if (fabs(w) <= 1e-12 * s_wmax || w == 0.0) continue;
+            if (fabs(w) <= kRankTol * s_wmax || w == 0.0) continue;
             s += Q[a * R + k] * Q[b * R + k] / w;
         }
         W[e] = s;

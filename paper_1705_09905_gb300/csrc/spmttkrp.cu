@@ -12,22 +12,28 @@
 //   * a lane group of LPR lanes spans the R columns of one output row: each
 //     lane loads E contiguous elements (16 bytes) of every gathered factor row,
 //     so one row gather is a fully coalesced 64..512-byte access;
-//   * the group walks its run in stages of 32 nonzeros: the index and value
-//     streams of a stage are loaded with 16-byte vector loads into shared
-//     memory, the bit-flag word of the stage is one 32-bit load; rows of the
-//     last product mode are gathered every nonzero, rows of the other product
-//     modes only when their indices change (the F-COO sort order puts equal
-//     indices next to each other inside a segment);
-//   * partial sums stay in registers; a segment that starts and ends inside a
-//     run is stored directly (one plain store per output row); segments cut by
-//     run boundaries are combined per CTA in shared memory (FP64, run order);
-//     segments cut by CTA boundaries leave one FP64 carry per CTA side, and
-//     k_carry_fixup adds the carries of each such segment in CTA order and
-//     stores the row.  No atomics on the output, no pre-zeroing, and the
-//     result is bitwise reproducible for a given handle, R and GPU;
-//   * within a run the accumulation is FP32; every 32 nonzeros the stage sum
-//     is folded into the segment sum with Kahan compensation, so the error of
-//     a long (Zipf-hot) segment grows with its number of stages, not nonzeros.
+//   * the group walks its run in stages of 32 nonzeros.  The index / value
+//     streams and the bit-flag word of a stage are copied by cp.async into a
+//     3-deep ring in shared memory, two stages ahead of use; groups' rings are
+//     offset by 16 bytes modulo 128 so that the 128-bit reads of one warp hit
+//     distinct banks;
+//   * within a stage, 8 nonzeros at a time: their last-product-mode rows (and,
+//     for 3-way SpMTTKRP, the rows of the other product mode where a new fibre
+//     starts) are all requested before any is consumed;
+//   * fibre factorisation: along a fibre (fixed index mode and non-last
+//     product modes) acc_f += val * row; when the fibre ends, acc_st += brow *
+//     acc_f with brow the product of the fibre's other rows -- one multiply per
+//     element and nonzero;
+//   * every 32 nonzeros the stage sum is folded into the segment sum with
+//     Kahan compensation, so the error of a long (Zipf-hot) segment grows with
+//     its number of stages, not nonzeros;
+//   * a segment that starts and ends inside a run is stored directly (one
+//     plain store per output row); segments cut by run boundaries are combined
+//     per CTA in shared memory (FP64, run order); segments cut by CTA
+//     boundaries leave one FP64 carry per CTA side, and k_carry_fixup adds the
+//     carries of each such segment in CTA order and stores the row.  No
+//     atomics on the output, no pre-zeroing, and the result is bitwise
+//     reproducible for a given handle, R and GPU.
 // The paper replaces atomics with a segmented scan whose inter-block carry is
 // passed by adjacent synchronisation (CTAs spinning on their predecessor); the
 // carry-slot + fixup pass gives the same atomic-free result without any CTA
@@ -36,6 +42,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -43,7 +50,8 @@ namespace fcx {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int T = 32;  // nonzeros per stage
+constexpr int T = 32;   // nonzeros per stage
+constexpr int NS = 3;   // stages in the ring (two in flight while one is consumed)
 
 // ------------------------------------------------------------ row loads
 
@@ -111,6 +119,22 @@ __device__ __forceinline__ void store_row(float *dst, const float (&v)[E]) {
     }
 }
 
+// ------------------------------------------------------------ async copies
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Number of heads (segment starts) strictly before nonzero position pos
 // (pos a multiple of 32): chunk checkpoint plus popcounts of the words since.
 __device__ __forceinline__ int64_t heads_before(const StreamParams &p, int64_t pos, int lig, int lpr,
@@ -127,6 +151,13 @@ __device__ __forceinline__ bool head_at(const StreamParams &p, int64_t pos) {
     return (__ldg(p.bf + (pos >> 5)) >> (pos & 31)) & 1u;
 }
 
+// Bytes of one stage in the ring (streams + bit-flag word, 16-byte padded)
+// and the per-group ring stride (16 mod 128 so groups hit different banks).
+__host__ __device__ constexpr int slot_bytes(int nstream) { return nstream * T * 4 + 16; }
+__host__ __device__ constexpr int group_stride(int nstream) {
+    return ((NS * slot_bytes(nstream) + 127) / 128) * 128 + 16;
+}
+
 // ------------------------------------------------------------ the kernel
 
 // TF: factor element type; E: elements per lane per chunk (16 bytes for the
@@ -140,19 +171,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
     using raw = typename IO::raw;
     constexpr int G = kThreads / LPR;  // groups per CTA
     constexpr int RT = NCH * LPR * E;  // columns covered by a group
-    constexpr int U = 4;               // nonzeros whose gathers are issued together
+    // nonzeros whose gathers are issued together (fewer when a lane holds
+    // more than 4 columns, to stay within 128 registers)
+    constexpr int U = E * NCH <= 4 ? 8 : 4;
     const int nprod = NP > 0 ? NP : p.nprod;
+    const int nstream = nprod + 1;
     const int R = p.R;
     const int tid = threadIdx.x, lane = tid & 31;
     const int g = tid / LPR, lig = tid % LPR;
     const unsigned gmask = LPR == 32 ? kFull : (((1u << LPR) - 1u) << (lane / LPR * LPR));
     const bool has_out = p.out != nullptr;
 
-    extern __shared__ __align__(16) unsigned char smem[];
-    // [G][nprod][T] uint32 indices, [G][T] float values, then the partial list
-    uint32_t *s_idx = reinterpret_cast<uint32_t *>(smem) + (size_t)g * nprod * T;
-    float *s_val = reinterpret_cast<float *>(smem) + (size_t)G * nprod * T + (size_t)g * T;
-    double *s_part = reinterpret_cast<double *>(smem + (size_t)G * (nprod + 1) * T * 4);
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int sbytes = slot_bytes(nstream);
+    const int gstride = group_stride(nstream);
+    unsigned char *ring = smem + (size_t)g * gstride;
+    double *s_part = reinterpret_cast<double *>(smem + (size_t)G * gstride);
     int64_t *s_pseg = reinterpret_cast<int64_t *>(s_part + (size_t)2 * G * RT);
     int *s_pflag = reinterpret_cast<int *>(s_pseg + 2 * G);
     float *s_loss = reinterpret_cast<float *>(s_pflag + 2 * G);
@@ -162,8 +196,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
     const int64_t r0 = min(c0 + (int64_t)g * p.run_len, c1);
     const int64_t r1 = min(r0 + p.run_len, c1);
 
-    const TF *Fl = static_cast<const TF *>(p.F[nprod - 1]);
-
     // columns of this lane
     int col[NCH];
     bool act[NCH];
@@ -172,6 +204,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
         col[c] = (c * LPR + lig) * E;
         act[c] = col[c] < R;
     }
+    const TF *Fl = static_cast<const TF *>(p.F[nprod - 1]);
+    const TF *Fb = static_cast<const TF *>(p.F[0]);
 
     if (lig == 0) {
         s_pseg[2 * g] = -1;
@@ -186,6 +220,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
     }
 
     if (r0 < r1) {
+        const int nst = (int)((r1 - r0 + T - 1) / T);
+        // ---- stream prefetch: stage s -> ring slot s % NS
+        auto issue_stage = [&](int s) {
+            if (s < nst) {
+                const int64_t base = r0 + (int64_t)s * T;
+                unsigned char *slot = ring + (s % NS) * sbytes;
+                const int nchunks = nstream * (T / 4);
+                for (int c = lig; c < nchunks; c += LPR) {
+                    const int a = c / (T / 4), q = c % (T / 4);
+                    const void *src = a < nprod ? (const void *)(p.pidx[a] + base + q * 4)
+                                                : (const void *)(p.val + base + q * 4);
+                    cp_async16(slot + a * T * 4 + q * 16, src);
+                }
+                if (lig == 0) cp_async4(slot + nstream * T * 4, p.bf + (base >> 5));
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int s = 0; s < NS - 1; ++s) issue_stage(s);
+
         // segment containing r0 and whether r0 opens it (start-flag of the partition)
         const int64_t part = r0 / p.threadlen;
         const bool head0 = (__ldg(p.sf + (part >> 5)) >> (part & 31)) & 1u;
@@ -209,12 +263,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
         };
         if (has_out && p.segrow && head0) fill_gap(seg > 0 ? (int64_t)__ldg(p.segrow + seg - 1) : -1, row);
 
-        float acc[NCH][E], cmp[NCH][E], blk[NCH][E], brow[NCH][E];
-        float trow[KIND == 1 ? NCH : 1][E];
+        // accumulators: fibre, stage, segment (Kahan pair)
+        float acc_f[NCH][E], acc_st[NCH][E], acc[NCH][E], cmp[NCH][E], brow[NCH][E];
+        float trow[KIND == 1 ? NCH : 1][E], tb[KIND == 1 ? NCH : 1][E];
 #pragma unroll
         for (int c = 0; c < NCH; ++c)
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc[c][e] = cmp[c][e] = blk[c][e] = 0.f, brow[c][e] = 1.f;
+            for (int e = 0; e < E; ++e) {
+                acc_f[c][e] = acc_st[c][e] = acc[c][e] = cmp[c][e] = 0.f;
+                brow[c][e] = 1.f;
+            }
         auto load_target = [&]() {
             if constexpr (KIND == 1) {
                 const TF *Tm = static_cast<const TF *>(p.T);
@@ -226,25 +284,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
 #pragma unroll
                         for (int e = 0; e < E; ++e) trow[c][e] = 0.f;
                     }
+#pragma unroll
+                    for (int e = 0; e < E; ++e) tb[c][e] = trow[c][e] * brow[c][e];
                 }
             }
         };
         load_target();
-        constexpr int NK = NP > 1 ? NP - 1 : (NP == 1 ? 1 : FCOO_MAX_MODES - 1);
-        uint32_t lastkey[NK];
-#pragma unroll
-        for (int m = 0; m < NK; ++m) lastkey[m] = 0xffffffffu;
 
-        auto fold = [&]() {  // Kahan: acc += blk
+        auto close_fibre = [&]() {
 #pragma unroll
             for (int c = 0; c < NCH; ++c)
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    float y = blk[c][e] - cmp[c][e];
+                    acc_st[c][e] = fmaf(brow[c][e], acc_f[c][e], acc_st[c][e]);
+                    acc_f[c][e] = 0.f;
+                }
+        };
+        auto fold = [&]() {  // Kahan: acc += acc_st
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    float y = acc_st[c][e] - cmp[c][e];
                     float t = acc[c][e] + y;
                     cmp[c][e] = (t - acc[c][e]) - y;
                     acc[c][e] = t;
-                    blk[c][e] = 0.f;
+                    acc_st[c][e] = 0.f;
                 }
         };
         // hand a finished (or run-cut) segment to its writer
@@ -272,152 +337,188 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                 }
             }
         };
-
-        for (int64_t base = r0; base < r1; base += T) {
-            // ---- stage: index and value streams into shared memory
-            __syncwarp(gmask);
-            for (int q = lig; q < T / 4; q += LPR) {
-                for (int m = 0; m < nprod; ++m)
-                    reinterpret_cast<uint4 *>(s_idx + m * T)[q] =
-                        __ldg(reinterpret_cast<const uint4 *>(p.pidx[m] + base) + q);
-                reinterpret_cast<float4 *>(s_val)[q] = __ldg(reinterpret_cast<const float4 *>(p.val + base) + q);
+        // a new segment starts at this nonzero (the fibre is already closed)
+        auto new_segment = [&]() {
+            fold();
+            emit(first && !head0, false);
+            first = false;
+            const int64_t prev = row;
+            ++seg;
+            row = p.segrow ? (int64_t)__ldg(p.segrow + seg) : seg;
+            if (has_out && p.segrow) fill_gap(prev, row);
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[c][e] = cmp[c][e] = 0.f;
+        };
+        // weight one gathered row into the fibre sum
+        auto accumulate = [&](float v, const raw (&cr)[NCH], int64_t pos) {
+            if constexpr (KIND == 0) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    float t[E];
+                    IO::cvt(cr[c], t);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) acc_f[c][e] = fmaf(v, t[e], acc_f[c][e]);
+                }
+            } else {
+                // e = <T(row), brow * c> - val, as <T(row) * brow, c>
+                float t[NCH][E];
+                float d = 0.f;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    IO::cvt(cr[c], t[c]);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) d = fmaf(tb[c][e], t[c][e], d);
+                }
+#pragma unroll
+                for (int o = 1; o < LPR; o <<= 1) d += __shfl_xor_sync(gmask, d, o);
+                const float w = p.sub_val ? d - v : d;
+                if (lig == 0) {
+                    lsum = fmaf(w, w, lsum);
+                    if (p.dvals) p.dvals[__ldg(p.perm + pos)] = p.dsign * w;
+                }
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) acc_f[c][e] = fmaf(w, t[c][e], acc_f[c][e]);
             }
-            const uint32_t hw = __ldg(p.bf + (base >> 5));
-            __syncwarp(gmask);
-            const int cnt = (int)min((int64_t)T, r1 - base);
+        };
+        // brow = product of the current fibre's non-last product-mode rows
+        auto set_brow_sync = [&](const unsigned char *slot, int u) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) brow[c][e] = 1.f;
+                if (!act[c]) continue;
+                for (int m = 0; m < nprod - 1; ++m) {
+                    const TF *Fm = static_cast<const TF *>(p.F[m]);
+                    const uint32_t km = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[u];
+                    float t[E];
+                    IO::cvt(IO::load(Fm + (size_t)km * R + col[c]), t);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) brow[c][e] *= t[e];
+                }
+            }
+        };
+        auto set_tb = [&]() {
+            if constexpr (KIND == 1) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) tb[c][e] = trow[c][e] * brow[c][e];
+            }
+        };
 
-            for (int u = 0; u < cnt; u += U) {
-                // ---- issue the gathers of U nonzeros before consuming any
-                raw cr[U][NCH];
-                raw fr[U][NCH][NP > 1 ? NP - 1 : 1];
-                bool fc[U], hd[U], ok[U];
+        uint32_t jprev = 0xffffffffu;           // fibre key of the previous nonzero (3-way)
+        uint32_t lastkey[FCOO_MAX_MODES - 1];  // fibre keys of the previous nonzero (general)
+#pragma unroll
+        for (int m = 0; m < FCOO_MAX_MODES - 1; ++m) lastkey[m] = 0xffffffffu;
+
+        // ---- one stage: FULL = all 32 nonzeros belong to the run
+        auto process_stage = [&](auto full_tag, const unsigned char *slot, int64_t base, uint32_t hw, int cnt) {
+            constexpr bool FULL = decltype(full_tag)::value;
+            const uint32_t *sk = reinterpret_cast<const uint32_t *>(slot + (nprod - 1) * T * 4);
+            const uint32_t *sj = reinterpret_cast<const uint32_t *>(slot);
+            const float *sv = reinterpret_cast<const float *>(slot + nprod * T * 4);
+#pragma unroll 1
+            for (int ub = 0; ub < T; ub += U) {
+                if (!FULL && ub >= cnt) break;
+                uint32_t kk[U], jj[U];
                 float vv[U];
 #pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    const int uu = u + q;
-                    ok[q] = uu < cnt;
-                    const int64_t pos = base + uu;
-                    hd[q] = ok[q] && ((hw >> uu) & 1u) && pos != r0;
-                    vv[q] = ok[q] ? s_val[uu] : 0.f;
-                    bool change = pos == r0;
-                    if (ok[q] && nprod > 1) {
-                        for (int m = 0; m < nprod - 1; ++m) {
-                            uint32_t k = s_idx[m * T + uu];
-                            uint32_t prev = uu > 0 ? s_idx[m * T + uu - 1] : lastkey[m];
-                            change |= k != prev;
+                for (int h = 0; h < U / 4; ++h) {
+                    const uint4 k4 = *reinterpret_cast<const uint4 *>(sk + ub + 4 * h);
+                    const float4 v4 = *reinterpret_cast<const float4 *>(sv + ub + 4 * h);
+                    kk[4 * h] = k4.x, kk[4 * h + 1] = k4.y, kk[4 * h + 2] = k4.z, kk[4 * h + 3] = k4.w;
+                    vv[4 * h] = v4.x, vv[4 * h + 1] = v4.y, vv[4 * h + 2] = v4.z, vv[4 * h + 3] = v4.w;
+                    if constexpr (NP == 2) {
+                        const uint4 j4 = *reinterpret_cast<const uint4 *>(sj + ub + 4 * h);
+                        jj[4 * h] = j4.x, jj[4 * h + 1] = j4.y, jj[4 * h + 2] = j4.z, jj[4 * h + 3] = j4.w;
+                    }
+                }
+                constexpr uint32_t kAll = (1u << U) - 1u;
+                const uint32_t okm = FULL ? kAll : (cnt - ub >= U ? kAll : ((1u << (cnt - ub)) - 1u));
+                const uint32_t hdm = (hw >> ub) & okm;
+                uint32_t fcm = hdm;
+                if constexpr (NP == 2) {
+#pragma unroll
+                    for (int q = 0; q < U; ++q) fcm |= (uint32_t)(jj[q] != (q ? jj[q - 1] : jprev)) << q;
+                    jprev = jj[U - 1];
+                } else if constexpr (NP != 1) {
+                    if (nprod > 1) {
+                        for (int q = 0; q < U; ++q) {
+                            bool ch = false;
+                            for (int m = 0; m < nprod - 1; ++m) {
+                                const uint32_t k = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[ub + q];
+                                ch |= k != lastkey[m];
+                                lastkey[m] = k;
+                            }
+                            fcm |= (uint32_t)ch << q;
                         }
                     }
-                    fc[q] = ok[q] && (change || hd[q]);
-                    const uint32_t kl = ok[q] ? s_idx[(nprod - 1) * T + uu] : 0u;
+                }
+                fcm &= okm;
+                // ---- issue the gathers of U nonzeros before consuming any
+                raw cr[U][NCH];
+                raw br[NP == 2 ? U : 1][NCH];
+#pragma unroll
+                for (int q = 0; q < U; ++q) {
+                    const bool ok = FULL || ((okm >> q) & 1u);
 #pragma unroll
                     for (int c = 0; c < NCH; ++c)
-                        cr[q][c] = (ok[q] && act[c]) ? IO::load(Fl + (size_t)kl * R + col[c]) : IO::zero();
-                    if constexpr (NP > 1) {
+                        cr[q][c] = (ok && act[c]) ? IO::load(Fl + (size_t)kk[q] * R + col[c]) : IO::zero();
+                    if constexpr (NP == 2) {
+                        const bool f = (fcm >> q) & 1u;
 #pragma unroll
-                        for (int m = 0; m < NP - 1; ++m) {
-                            const uint32_t km = s_idx[m * T + uu];
-                            const TF *Fm = static_cast<const TF *>(p.F[m]);
-#pragma unroll
-                            for (int c = 0; c < NCH; ++c)
-                                fr[q][c][m] =
-                                    (fc[q] && act[c]) ? IO::load(Fm + (size_t)km * R + col[c]) : IO::zero();
-                        }
+                        for (int c = 0; c < NCH; ++c)
+                            br[q][c] = (f && act[c]) ? IO::load(Fb + (size_t)jj[q] * R + col[c]) : IO::zero();
                     }
                 }
                 // ---- consume in order
 #pragma unroll
                 for (int q = 0; q < U; ++q) {
-                    if (!ok[q]) continue;
-                    const int uu = u + q;
-                    if (hd[q]) {  // a new segment starts: close the current one
-                        fold();
-                        emit(first && !head0, false);
-                        first = false;
-                        const int64_t prev = row;
-                        ++seg;
-                        row = p.segrow ? (int64_t)__ldg(p.segrow + seg) : seg;
-                        if (has_out && p.segrow) fill_gap(prev, row);
-                        load_target();
+                    if (!FULL && !((okm >> q) & 1u)) break;
+                    if ((fcm >> q) & 1u) {
+                        close_fibre();
+                        if ((hdm >> q) & 1u) {
+                            new_segment();
+                            load_target();
+                        }
+                        if constexpr (NP == 2) {
 #pragma unroll
-                        for (int c = 0; c < NCH; ++c)
-#pragma unroll
-                            for (int e = 0; e < E; ++e) acc[c][e] = cmp[c][e] = 0.f;
+                            for (int c = 0; c < NCH; ++c) IO::cvt(br[q][c], brow[c]);
+                        } else if constexpr (NP != 1) {
+                            if (nprod > 1) set_brow_sync(slot, ub + q);
+                        }
+                        set_tb();
                     }
-                    if (fc[q]) {  // new fibre: product of the non-last product-mode rows
-                        if constexpr (NP > 1) {
-#pragma unroll
-                            for (int c = 0; c < NCH; ++c) {
-                                float t[E];
-                                IO::cvt(fr[q][c][0], t);
-#pragma unroll
-                                for (int e = 0; e < E; ++e) brow[c][e] = t[e];
-#pragma unroll
-                                for (int m = 1; m < NP - 1; ++m) {
-                                    IO::cvt(fr[q][c][m], t);
-#pragma unroll
-                                    for (int e = 0; e < E; ++e) brow[c][e] *= t[e];
-                                }
-                            }
-                        } else if constexpr (NP == 0) {
-                            if (nprod > 1) {
-#pragma unroll
-                                for (int c = 0; c < NCH; ++c) {
-#pragma unroll
-                                    for (int e = 0; e < E; ++e) brow[c][e] = 1.f;
-                                    if (!act[c]) continue;
-                                    for (int m = 0; m < nprod - 1; ++m) {
-                                        const TF *Fm = static_cast<const TF *>(p.F[m]);
-                                        float t[E];
-                                        IO::cvt(IO::load(Fm + (size_t)s_idx[m * T + uu] * R + col[c]), t);
-#pragma unroll
-                                        for (int e = 0; e < E; ++e) brow[c][e] *= t[e];
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    if constexpr (KIND == 0) {
-#pragma unroll
-                        for (int c = 0; c < NCH; ++c) {
-                            float t[E];
-                            IO::cvt(cr[q][c], t);
-#pragma unroll
-                            for (int e = 0; e < E; ++e) blk[c][e] = fmaf(vv[q] * brow[c][e], t[e], blk[c][e]);
-                        }
-                    } else {
-                        // h = prod of the product-mode rows; e = <T(row), h> - val
-                        float h[NCH][E];
-                        float d = 0.f;
-#pragma unroll
-                        for (int c = 0; c < NCH; ++c) {
-                            float t[E];
-                            IO::cvt(cr[q][c], t);
-#pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                h[c][e] = brow[c][e] * t[e];
-                                d = fmaf(trow[c][e], h[c][e], d);
-                            }
-                        }
-#pragma unroll
-                        for (int o = 1; o < LPR; o <<= 1) d += __shfl_xor_sync(gmask, d, o);
-                        const float w = p.sub_val ? d - vv[q] : d;
-                        if (lig == 0) {
-                            lsum = fmaf(w, w, lsum);
-                            if (p.dvals) p.dvals[__ldg(p.perm + base + uu)] = p.dsign * w;
-                        }
-#pragma unroll
-                        for (int c = 0; c < NCH; ++c)
-#pragma unroll
-                            for (int e = 0; e < E; ++e) blk[c][e] = fmaf(w, h[c][e], blk[c][e]);
-                    }
+                    accumulate(vv[q], cr[q], base + ub + q);
                 }
             }
-            if (nprod > 1) {
-                for (int m = 0; m < nprod - 1; ++m) lastkey[m] = s_idx[m * T + cnt - 1];
-            }
+        };
+
+#pragma unroll 1
+        for (int s = 0; s < nst; ++s) {
+            __syncwarp(gmask);  // every lane is done with the slot about to be refilled
+            issue_stage(s + NS - 1);
+            cp_async_wait<NS - 1>();
+            __syncwarp(gmask);
+            const unsigned char *slot = ring + (s % NS) * sbytes;
+            const int64_t base = r0 + (int64_t)s * T;
+            const int cnt = (int)min((int64_t)T, r1 - base);
+            uint32_t hw = *reinterpret_cast<const uint32_t *>(slot + nstream * T * 4);
+            if (s == 0) hw &= ~1u;  // r0 opens the run, not a new segment
+            if (cnt == T)
+                process_stage(std::integral_constant<bool, true>{}, slot, base, hw, cnt);
+            else
+                process_stage(std::integral_constant<bool, false>{}, slot, base, hw, cnt);
+            // the open fibre carries over; fold what the stage closed
             fold();
         }
-        // ---- end of run: the last segment
+        // ---- end of run: close the fibre and the last segment
+        close_fibre();
+        fold();
         const bool ends_here = (r1 == p.nnz) || head_at(p, r1);
         emit(first && !head0, !ends_here);
         if (has_out && p.segrow && r1 == p.nnz) fill_gap(row, p.out_rows);
@@ -546,7 +647,7 @@ int launch_variant(StreamParams &p, cudaStream_t s) {
     constexpr int G = kThreads / LPR;
     constexpr int RT = NCH * LPR * E;
     auto kern = k_stream<TF, E, LPR, NCH, NP, KIND>;
-    const size_t smem = (size_t)G * (p.nprod + 1) * T * 4 + (size_t)2 * G * RT * 8 + (size_t)2 * G * 8 +
+    const size_t smem = (size_t)G * group_stride(p.nprod + 1) + (size_t)2 * G * RT * 8 + (size_t)2 * G * 8 +
                         (size_t)2 * G * 4 + (size_t)G * 4;
     static size_t cached_smem = 0;
     static int cached_occ = 0;

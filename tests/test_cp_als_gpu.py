@@ -83,7 +83,9 @@ def test_pseudo_inverse_fallback(fc, oracle):
     F, lam, fits, npinv = oracle.cp_als(T.dims, T.idx_u32(), T.val.double().numpy(),
                                         [f.double().numpy() for f in init], 1)
     assert s["npinv"] == npinv > 0
-    assert abs(s["fit"] - fits[0]) <= 1e-5
+    # this tensor is fitted exactly (fit 1): the Grams identity for the fit then
+    # subtracts nearly equal terms, so FP32 inputs (~1e-7) give ~sqrt(1e-7) there
+    assert abs(s["fit"] - fits[0]) <= 1e-3
     for k in range(3):
         assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 1e-4
 
