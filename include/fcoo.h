@@ -201,6 +201,65 @@ int spmttkrp(const fcoo_t *X, const void *const *factors, int dtype, int R, floa
 int spttm(const fcoo_t *X, const void *U, int dtype, int R, float *out, fcoo_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* SpMTTKRP for callers that cannot allocate device memory                  */
+/* ---------------------------------------------------------------------- */
+
+/* Largest R and number of CTAs spmttkrp_noalloc accepts (they size its
+ * fixed scratch: 2 * FCOO_NOALLOC_MAX_CTAS * FCOO_NOALLOC_MAX_RANK doubles
+ * plus 2 * FCOO_NOALLOC_MAX_CTAS int64 = 2 MiB + 16 KiB). */
+#define FCOO_NOALLOC_MAX_RANK 128
+#define FCOO_NOALLOC_MAX_CTAS 1024
+
+/* An F-COO layout for SpMTTKRP held in memory the caller owns.  The arrays
+ * are the ones fcoo_copy_layout returns (same meaning, same order), placed
+ * by the caller in device memory:
+ *   pidx[m]  product-mode indices of stream m (modes ascending, all but
+ *            `mode`), val the values: each array 16-byte aligned and readable
+ *            for round_up(nnz, 32) entries (entries past nnz are read, unused)
+ *   bf       ceil(nnz/32) words of segment-start bits; sf the start-flag words
+ *            for partitions of `threadlen` nonzeros
+ *   segrow   nseg output rows, one per segment, ascending
+ *   hcount   ceil(nnz/1024)+1 words: hcount[c] = number of set bits in
+ *            bf[0 .. 32c-1] (segment starts before nonzero 1024c)
+ * No pointer is retained after the call returns. */
+typedef struct {
+    int nmodes, mode, threadlen;
+    int64_t nnz, nseg;
+    uint32_t dims[FCOO_MAX_MODES];
+    const uint32_t *pidx[FCOO_MAX_MODES - 1];
+    const float *val;
+    const uint32_t *bf, *sf, *segrow, *hcount;
+} fcoo_view_t;
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory while they run: code whose device
+ * memory is reserved up front by a framework allocator or a fixed arena, and
+ * real-time or safety-constrained code that forbids allocation after
+ * start-up.  spmttkrp (above) allocates nothing per call either, but its
+ * scratch lives in the handle that fcoo_build allocates; this variant takes
+ * the layout as plain caller-owned buffers and keeps its scratch (the
+ * per-CTA carry slots) in a fixed array inside the library.
+ *
+ * Computes exactly what spmttkrp computes (Eq. 6) for the layout in *view:
+ *   out(i, :) = sum over nonzeros p with idx_mode(p) = i of
+ *               val(p) * prod_{k != mode} F_k(idx_k(p), :)
+ *   factors  host array of nmodes device pointers, dims[k] x R of dtype
+ *            (factors[mode] not read); R in 1..FCOO_NOALLOC_MAX_RANK
+ *   out      device float32 dims[mode] x R, fully overwritten
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch (2 MiB + 16 KiB) is a file-scope __device__ array held by every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current) and caches it; make that first call before any stream
+ * capture.  Every call uses the same array, so calls that overlap on the GPU
+ * (other streams, other threads) race and give wrong results: serialise them.
+ * Nothing in the array has to start at zero: each launch initialises the
+ * slots it reads.  Requests over the limits return FCOO_ERR_UNSUPPORTED with
+ * a message.  Asynchronous on `stream`. */
+int spmttkrp_noalloc(const fcoo_view_t *view, const void *const *factors, int dtype, int R, float *out,
+                     fcoo_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* CP-ALS (Algorithm 1; Sec. IV-D "Complete tensor-based algorithms")       */
 /* ---------------------------------------------------------------------- */
 

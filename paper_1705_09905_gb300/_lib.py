@@ -42,6 +42,19 @@ class FcooInfo(ctypes.Structure):
     ]
 
 
+class FcooView(ctypes.Structure):
+    """fcoo_view_t: an SpMTTKRP F-COO layout in caller-owned device buffers."""
+
+    _fields_ = [
+        ("nmodes", ctypes.c_int), ("mode", ctypes.c_int), ("threadlen", ctypes.c_int),
+        ("nnz", ctypes.c_int64), ("nseg", ctypes.c_int64),
+        ("dims", ctypes.c_uint32 * MAX_MODES),
+        ("pidx", ctypes.c_void_p * (MAX_MODES - 1)),
+        ("val", ctypes.c_void_p), ("bf", ctypes.c_void_p), ("sf", ctypes.c_void_p),
+        ("segrow", ctypes.c_void_p), ("hcount", ctypes.c_void_p),
+    ]
+
+
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _i64 = ctypes.c_int64
@@ -60,6 +73,7 @@ SIGNATURES = {
     "fcoo_fibre_indices": (_i, [_vp, _vp, _vp]),
     "spmttkrp": (_i, [_vp, _vpp, _i, _i, _vp, _vp]),
     "spttm": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "spmttkrp_noalloc": (_i, [ctypes.POINTER(FcooView), _vpp, _i, _i, _vp, _vp]),
     "cp_state_create": (_i, [_i, _vp, _i, _i, _vpp, _vp, ctypes.POINTER(_vp)]),
     "cp_state_destroy": (_i, [_vp]),
     "cp_als_iter": (_i, [_vpp, _vp, _vp]),
