@@ -307,7 +307,7 @@ def bench_cp_als(fc, Xs, dims, sweeps, R=64):
         torch.cuda.synchronize()
         s = st.stats()
         res[name] = {"s_per_iter": a.elapsed_time(b) / 1e3 / (sweeps - 1), "fit": s["fit"], "iters": s["iters"],
-                     "factors": [st.factor(k) for k in range(3)]}
+                     "pinv_solves": s["npinv"], "factors": [st.factor(k) for k in range(3)]}
         st.close()
     rel = [float(torch.linalg.norm(res["bf16"]["factors"][k] - res["fp32"]["factors"][k]) /
                  torch.linalg.norm(res["fp32"]["factors"][k])) for k in range(3)]

@@ -275,11 +275,13 @@ int cp_state_destroy(cp_state_t *st);
 
 /* One full sweep of Algorithm 1 over all modes n = 0..N-1:
  *   M   = SpMTTKRP_n(X, F)                       (Eq. 6, FP32 accumulation)
- *   V   = Hadamard product over k != n of F_k^T F_k  (FP64 sums of FP32 Gram
- *         partials of the stored factors: ~1e-7 relative accuracy)
- *   F_n = M V^dagger   (FP64 Cholesky; if a pivot is <= 1e-6 * max diag(V),
- *                       i.e. below the accuracy of V, the eigen-decomposition
- *                       pseudo-inverse that drops eigenvalues <= 1e-6 * max |eig|)
+ *   V   = Hadamard product over k != n of F_k^T F_k  (Grams of the stored
+ *         factors from compensated FP32 partial sums added in FP64)
+ *   F_n = M V^dagger   (FP64 Cholesky; if a pivot is <= 1e-12 * max diag(V),
+ *                       the eigen-decomposition pseudo-inverse that drops
+ *                       eigenvalues <= 1e-12 * max |eig|; the product with M in
+ *                       compensated FP32 against the inverse split in two
+ *                       FP32 parts)
  *   lambda = column 2-norms of F_n; F_n columns divided by them (a zero
  *            column keeps lambda 0 and is left as it is)
  * then the fit 1 - sqrt(max(0, |X|^2 + |Xhat|^2 - 2<X,Xhat>)) / |X|.

@@ -47,11 +47,17 @@ namespace {
 constexpr int kRowsPerBlock = 128;  // rows per CTA in the I x R kernels
 constexpr int kSolveThreads = 256;
 // Relative size below which a Cholesky pivot or an eigenvalue of V counts as
-// zero.  The Grams are FP64 sums of FP32 partials of FP32/BF16-stored
-// factors, accurate to ~1e-7 relative; a smaller threshold would let rounding
-// noise pass for rank.  (The FP64 oracle, whose Grams are exact to 1e-16,
-// uses 1e-12.)
-constexpr double kRankTol = 1e-6;
+// zero, as in the FP64 oracle.  It is meaningful here because the Grams are
+// compensated (Dot2) sums of the stored factors, accurate to ~1e-13: with
+// plain FP32 partial sums (~1e-7) rounding noise passed for rank.
+constexpr double kRankTol = 1e-12;
+
+// W (FP64) -> Wf[0 .. R*R) = FP32 high part, Wf[R*R .. 2*R*R) = FP32 remainder.
+__device__ __forceinline__ void split_store(float *Wf, int RR, int e, double w) {
+    const float hi = (float)w;
+    Wf[e] = hi;
+    Wf[RR + e] = (float)(w - (double)hi);
+}
 
 int64_t max_blocks(int64_t max_dim) { return ceil_div(max_dim, kRowsPerBlock); }
 
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, dou
         __syncthreads();
         for (int e = tid; e < R * R; e += nt) {
             W[e] = V[e];
-            Wf[e] = (float)V[e];
+            split_store(Wf, R * R, e, V[e]);
         }
         return;
     }
@@ -248,20 +254,43 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, dou
         W[e] = s;
     }
     __syncthreads();
-    for (int e = tid; e < R * R; e += nt) Wf[e] = (float)W[e];
+    for (int e = tid; e < R * R; e += nt) split_store(Wf, R * R, e, W[e]);
 }
 
 // ---------------------------------------------------------------- I x R kernels
 
-// Fu = M * W (FP32), one CTA per kRowsPerBlock rows; column sums of squares
-// of Fu per CTA into part[blk * R + c] (FP64).
+// Compensated FP32 dot product (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005, algorithm Dot2): the product is split
+// exactly with an FMA, the running sum with TwoSum, and all rounding errors
+// are collected in c, so s + c carries about twice the FP32 precision.  The
+// _rn intrinsics keep the compiler from contracting the error terms.
+struct Dot2 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float pe = fmaf(a, b, -p);  // a * b == p + pe exactly
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // s + p == t + se
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(se, pe));
+    }
+    __device__ __forceinline__ void add_small(float a, float b) { c = fmaf(a, b, c); }
+};
+
+// Fu = M * W, one CTA per kRowsPerBlock rows, W = Wf_hi + Wf_lo (the FP64
+// inverse split into two FP32 parts) and Dot2 accumulation, so the result is
+// accurate to about one FP32 rounding even when V is ill-conditioned (a plain
+// FP32 product would lose about cond(V) ulps).  Column sums of squares of Fu
+// per CTA into part[blk * R + c] (FP64).
 __global__ void k_apply(const float *M, const float *Wf, int64_t I, int R, float *Fu, double *part) {
     extern __shared__ __align__(16) float sm[];
-    float *sW = sm;            // R x R
-    float *sM = sm + R * R;    // kRowsPerBlock x R
+    float *sWh = sm;                // R x R
+    float *sWl = sm + R * R;        // R x R
+    float *sM = sm + 2 * R * R;     // kRowsPerBlock x R
     const int64_t i0 = (int64_t)blockIdx.x * kRowsPerBlock;
     const int rows = (int)min((int64_t)kRowsPerBlock, I - i0);
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) sW[e] = Wf[e];
+    for (int e = threadIdx.x; e < 2 * R * R; e += blockDim.x) sWh[e] = Wf[e];
     for (int e = threadIdx.x; e < rows * R; e += blockDim.x) sM[e] = M[i0 * R + e];
     __syncthreads();
     // blockDim.x is a multiple of R: thread (r0, c) handles column c of rows r0, r0 + step, ...
@@ -269,8 +298,13 @@ __global__ void k_apply(const float *M, const float *Wf, int64_t I, int R, float
     __shared__ double red[1024];
     double sq = 0.0;
     for (int r = r0; r < rows; r += step) {
-        float s = 0.f;
-        for (int k = 0; k < R; ++k) s = fmaf(sM[r * R + k], sW[k * R + c], s);
+        Dot2 d;
+        for (int k = 0; k < R; ++k) {
+            const float m = sM[r * R + k];
+            d.add(m, sWh[k * R + c]);
+            d.add_small(m, sWl[k * R + c]);
+        }
+        const float s = __fadd_rn(d.s, d.c);
         Fu[(i0 + r) * R + c] = s;
         sq += (double)s * s;
     }
@@ -326,8 +360,10 @@ __global__ void k_normalize(const float *Fu, const double *lambda, int64_t I, in
     }
 }
 
-// Per-CTA Gram partial of the stored factor rows [i0, i0 + rows): FP32 sums
-// of kRowsPerBlock products, written as FP64.
+// Per-CTA Gram partial of the stored factor rows [i0, i0 + rows): Dot2
+// (compensated FP32) sums of kRowsPerBlock products, written as FP64, so the
+// Gram of the stored factor is accurate to ~1e-13 relative and rank decisions
+// on V see the factors, not the summation error.
 template <typename TF>
 __global__ void k_gram_part(const TF *F, int64_t I, int R, double *part) {
     extern __shared__ __align__(16) float sF[];
@@ -337,9 +373,9 @@ __global__ void k_gram_part(const TF *F, int64_t I, int R, double *part) {
     __syncthreads();
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
         const int a = e / R, b = e % R;
-        float s = 0.f;
-        for (int r = 0; r < rows; ++r) s = fmaf(sF[r * R + a], sF[r * R + b], s);
-        part[(int64_t)blockIdx.x * R * R + e] = s;
+        Dot2 d;
+        for (int r = 0; r < rows; ++r) d.add(sF[r * R + a], sF[r * R + b]);
+        part[(int64_t)blockIdx.x * R * R + e] = (double)d.s + (double)d.c;
     }
 }
 
@@ -454,7 +490,7 @@ int mode_update(const fcoo_t *X, cp_state_t *st, int n, bool last, cudaStream_t 
     // Fu = M W, column norms
     const int nb = (int)ceil_div(I, kRowsPerBlock);
     const int threads = R >= 256 ? R : (256 / R) * R;  // a multiple of R
-    const size_t smem = ((size_t)R * R + (size_t)kRowsPerBlock * R) * 4;
+    const size_t smem = ((size_t)2 * R * R + (size_t)kRowsPerBlock * R) * 4;
     FCOO_CUDA(cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_apply<<<nb, threads, smem, s>>>(st->M, st->Wf, I, R, st->Fu, st->part);
     FCOO_CUDA(cudaGetLastError());
@@ -512,7 +548,7 @@ extern "C" int cp_state_create(int nmodes, const uint32_t *dims, int R, int dtyp
     for (int k = 0; k < nmodes; ++k) oG[k] = take((size_t)R * R * 8);
     size_t oL = take(R * 8), oM = take((size_t)st->max_dim * R * 4), oFu = take((size_t)st->max_dim * R * 4);
     size_t oV = take((size_t)R * R * 8), oQ = take((size_t)R * R * 8), oW = take((size_t)R * R * 8);
-    size_t oWf = take((size_t)R * R * 4);
+    size_t oWf = take((size_t)2 * R * R * 4);
     size_t oP = take((size_t)std::max<int64_t>(nbmax * R * R, 4096) * 8);
     size_t oS = take(8 * 8), oFl = take(16);
     cudaError_t e = dev_alloc(&st->base, off);

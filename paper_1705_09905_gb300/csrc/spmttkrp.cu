@@ -20,10 +20,12 @@
 //   * within a stage, 8 nonzeros at a time: their last-product-mode rows (and,
 //     for 3-way SpMTTKRP, the rows of the other product mode where a new fibre
 //     starts) are all requested before any is consumed;
-//   * fibre factorisation: along a fibre (fixed index mode and non-last
-//     product modes) acc_f += val * row; when the fibre ends, acc_st += brow *
-//     acc_f with brow the product of the fibre's other rows -- one multiply per
-//     element and nonzero;
+//   * the rows of the non-last product modes change only where a new fibre
+//     starts (fixed index mode and non-last product modes): their product brow
+//     is kept in registers and replaced by a predicated select, and each
+//     nonzero adds (val * brow) * row with the paired FP32 instructions
+//     (FMUL2 / FFMA2, two elements per instruction); only blocks of 8
+//     nonzeros that contain a segment start take a branch;
 //   * every 32 nonzeros the stage sum is folded into the segment sum with
 //     Kahan compensation, so the error of a long (Zipf-hot) segment grows with
 //     its number of stages, not nonzeros;
@@ -204,6 +206,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
         col[c] = (c * LPR + lig) * E;
         act[c] = col[c] < R;
     }
+    // loads use a clamped column so that lanes past R read valid memory
+    // unconditionally (their sums are never stored)
+    int colc[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) colc[c] = act[c] ? col[c] : 0;
     const TF *Fl = static_cast<const TF *>(p.F[nprod - 1]);
     const TF *Fb = static_cast<const TF *>(p.F[0]);
 
@@ -263,14 +270,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
         };
         if (has_out && p.segrow && head0) fill_gap(seg > 0 ? (int64_t)__ldg(p.segrow + seg - 1) : -1, row);
 
-        // accumulators: fibre, stage, segment (Kahan pair)
-        float acc_f[NCH][E], acc_st[NCH][E], acc[NCH][E], cmp[NCH][E], brow[NCH][E];
-        float trow[KIND == 1 ? NCH : 1][E], tb[KIND == 1 ? NCH : 1][E];
+        // accumulators: stage sum, segment sum (Kahan pair); brow = product of
+        // the current fibre's non-last product-mode rows
+        float acc_st[NCH][E], acc[NCH][E], cmp[NCH][E], brow[NCH][E];
+        float trow[KIND == 1 ? NCH : 1][E];
 #pragma unroll
         for (int c = 0; c < NCH; ++c)
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                acc_f[c][e] = acc_st[c][e] = acc[c][e] = cmp[c][e] = 0.f;
+                acc_st[c][e] = acc[c][e] = cmp[c][e] = 0.f;
                 brow[c][e] = 1.f;
             }
         auto load_target = [&]() {
@@ -282,24 +290,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                         IO::cvt(IO::load(Tm + (size_t)row * R + col[c]), trow[c]);
                     } else {
 #pragma unroll
-                        for (int e = 0; e < E; ++e) trow[c][e] = 0.f;
+                        for (int e = 0; e < E; ++e) trow[c][e] = 0.f;  // masks the clamped lanes
                     }
-#pragma unroll
-                    for (int e = 0; e < E; ++e) tb[c][e] = trow[c][e] * brow[c][e];
                 }
             }
         };
         load_target();
 
-        auto close_fibre = [&]() {
-#pragma unroll
-            for (int c = 0; c < NCH; ++c)
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    acc_st[c][e] = fmaf(brow[c][e], acc_f[c][e], acc_st[c][e]);
-                    acc_f[c][e] = 0.f;
-                }
-        };
         auto fold = [&]() {  // Kahan: acc += acc_st
 #pragma unroll
             for (int c = 0; c < NCH; ++c)
@@ -337,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                 }
             }
         };
-        // a new segment starts at this nonzero (the fibre is already closed)
+        // a new segment starts at this nonzero
         auto new_segment = [&]() {
             fold();
             emit(first && !head0, false);
@@ -350,27 +347,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
             for (int c = 0; c < NCH; ++c)
 #pragma unroll
                 for (int e = 0; e < E; ++e) acc[c][e] = cmp[c][e] = 0.f;
+            load_target();
         };
-        // weight one gathered row into the fibre sum
+        // acc_st += w * (brow * row), w = val (KIND 0) or the residual weight
+        // (KIND 1); element pairs go through the paired FP32 instructions
         auto accumulate = [&](float v, const raw (&cr)[NCH], int64_t pos) {
+            float t[NCH][E];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) IO::cvt(cr[c], t[c]);
             if constexpr (KIND == 0) {
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) {
-                    float t[E];
-                    IO::cvt(cr[c], t);
+                    if constexpr (E % 2 == 0) {
+                        const float2 v2 = make_float2(v, v);
 #pragma unroll
-                    for (int e = 0; e < E; ++e) acc_f[c][e] = fmaf(v, t[e], acc_f[c][e]);
+                        for (int e = 0; e < E; e += 2) {
+                            const float2 s = __fmul2_rn(v2, make_float2(brow[c][e], brow[c][e + 1]));
+                            const float2 a = __ffma2_rn(s, make_float2(t[c][e], t[c][e + 1]),
+                                                        make_float2(acc_st[c][e], acc_st[c][e + 1]));
+                            acc_st[c][e] = a.x;
+                            acc_st[c][e + 1] = a.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) acc_st[c][e] = fmaf(v * brow[c][e], t[c][e], acc_st[c][e]);
+                    }
                 }
             } else {
-                // e = <T(row), brow * c> - val, as <T(row) * brow, c>
-                float t[NCH][E];
+                // h = brow * row; e = <T(row), h> - val; acc_st += e * h
+                float h[NCH][E];
                 float d = 0.f;
 #pragma unroll
-                for (int c = 0; c < NCH; ++c) {
-                    IO::cvt(cr[c], t[c]);
+                for (int c = 0; c < NCH; ++c)
 #pragma unroll
-                    for (int e = 0; e < E; ++e) d = fmaf(tb[c][e], t[c][e], d);
-                }
+                    for (int e = 0; e < E; ++e) {
+                        h[c][e] = brow[c][e] * t[c][e];
+                        d = fmaf(trow[c][e], h[c][e], d);
+                    }
 #pragma unroll
                 for (int o = 1; o < LPR; o <<= 1) d += __shfl_xor_sync(gmask, d, o);
                 const float w = p.sub_val ? d - v : d;
@@ -381,32 +394,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
 #pragma unroll
                 for (int c = 0; c < NCH; ++c)
 #pragma unroll
-                    for (int e = 0; e < E; ++e) acc_f[c][e] = fmaf(w, t[c][e], acc_f[c][e]);
+                    for (int e = 0; e < E; ++e) acc_st[c][e] = fmaf(w, h[c][e], acc_st[c][e]);
             }
         };
-        // brow = product of the current fibre's non-last product-mode rows
+        // brow from the rows of the non-last product modes (general N)
         auto set_brow_sync = [&](const unsigned char *slot, int u) {
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) brow[c][e] = 1.f;
-                if (!act[c]) continue;
                 for (int m = 0; m < nprod - 1; ++m) {
                     const TF *Fm = static_cast<const TF *>(p.F[m]);
                     const uint32_t km = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[u];
                     float t[E];
-                    IO::cvt(IO::load(Fm + (size_t)km * R + col[c]), t);
+                    IO::cvt(IO::load(Fm + (size_t)km * R + colc[c]), t);
 #pragma unroll
                     for (int e = 0; e < E; ++e) brow[c][e] *= t[e];
                 }
-            }
-        };
-        auto set_tb = [&]() {
-            if constexpr (KIND == 1) {
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-#pragma unroll
-                    for (int e = 0; e < E; ++e) tb[c][e] = trow[c][e] * brow[c][e];
             }
         };
 
@@ -440,26 +444,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                 constexpr uint32_t kAll = (1u << U) - 1u;
                 const uint32_t okm = FULL ? kAll : (cnt - ub >= U ? kAll : ((1u << (cnt - ub)) - 1u));
                 const uint32_t hdm = (hw >> ub) & okm;
-                uint32_t fcm = hdm;
+                // fibre starts: a change of the non-last product-mode indices, or a segment head
+                bool fc[U];
                 if constexpr (NP == 2) {
 #pragma unroll
-                    for (int q = 0; q < U; ++q) fcm |= (uint32_t)(jj[q] != (q ? jj[q - 1] : jprev)) << q;
+                    for (int q = 0; q < U; ++q) fc[q] = jj[q] != (q ? jj[q - 1] : jprev) || ((hdm >> q) & 1u);
                     jprev = jj[U - 1];
-                } else if constexpr (NP != 1) {
-                    if (nprod > 1) {
-                        for (int q = 0; q < U; ++q) {
-                            bool ch = false;
-                            for (int m = 0; m < nprod - 1; ++m) {
-                                const uint32_t k = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[ub + q];
-                                ch |= k != lastkey[m];
-                                lastkey[m] = k;
-                            }
-                            fcm |= (uint32_t)ch << q;
+                } else if constexpr (NP == 1) {
+#pragma unroll
+                    for (int q = 0; q < U; ++q) fc[q] = false;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        bool ch = (hdm >> q) & 1u;
+                        for (int m = 0; m < nprod - 1; ++m) {
+                            const uint32_t k = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[ub + q];
+                            ch |= k != lastkey[m];
+                            lastkey[m] = k;
                         }
+                        fc[q] = ch;
                     }
                 }
-                fcm &= okm;
-                // ---- issue the gathers of U nonzeros before consuming any
+                // ---- issue the gathers of U nonzeros before consuming any;
+                // clamped columns make every load of an in-range nonzero valid
                 raw cr[U][NCH];
                 raw br[NP == 2 ? U : 1][NCH];
 #pragma unroll
@@ -467,33 +474,46 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                     const bool ok = FULL || ((okm >> q) & 1u);
 #pragma unroll
                     for (int c = 0; c < NCH; ++c)
-                        cr[q][c] = (ok && act[c]) ? IO::load(Fl + (size_t)kk[q] * R + col[c]) : IO::zero();
+                        cr[q][c] = ok ? IO::load(Fl + (size_t)kk[q] * R + colc[c]) : IO::zero();
                     if constexpr (NP == 2) {
-                        const bool f = (fcm >> q) & 1u;
 #pragma unroll
                         for (int c = 0; c < NCH; ++c)
-                            br[q][c] = (f && act[c]) ? IO::load(Fb + (size_t)jj[q] * R + col[c]) : IO::zero();
+                            br[q][c] = (ok && fc[q]) ? IO::load(Fb + (size_t)jj[q] * R + colc[c]) : IO::zero();
                     }
                 }
-                // ---- consume in order
+                if (FULL && hdm == 0) {
+                    // ---- fast path: no segment starts in these U nonzeros
 #pragma unroll
-                for (int q = 0; q < U; ++q) {
-                    if (!FULL && !((okm >> q) & 1u)) break;
-                    if ((fcm >> q) & 1u) {
-                        close_fibre();
-                        if ((hdm >> q) & 1u) {
-                            new_segment();
-                            load_target();
-                        }
+                    for (int q = 0; q < U; ++q) {
                         if constexpr (NP == 2) {
 #pragma unroll
-                            for (int c = 0; c < NCH; ++c) IO::cvt(br[q][c], brow[c]);
+                            for (int c = 0; c < NCH; ++c) {
+                                float t[E];
+                                IO::cvt(br[q][c], t);
+#pragma unroll
+                                for (int e = 0; e < E; ++e) brow[c][e] = fc[q] ? t[e] : brow[c][e];
+                            }
                         } else if constexpr (NP != 1) {
-                            if (nprod > 1) set_brow_sync(slot, ub + q);
+                            if (fc[q]) set_brow_sync(slot, ub + q);
                         }
-                        set_tb();
+                        accumulate(vv[q], cr[q], base + ub + q);
                     }
-                    accumulate(vv[q], cr[q], base + ub + q);
+                } else {
+                    // ---- general path: segment starts and / or a ragged tail
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        if (!FULL && !((okm >> q) & 1u)) break;
+                        if ((hdm >> q) & 1u) new_segment();
+                        if (fc[q]) {
+                            if constexpr (NP == 2) {
+#pragma unroll
+                                for (int c = 0; c < NCH; ++c) IO::cvt(br[q][c], brow[c]);
+                            } else if constexpr (NP != 1) {
+                                set_brow_sync(slot, ub + q);
+                            }
+                        }
+                        accumulate(vv[q], cr[q], base + ub + q);
+                    }
                 }
             }
         };
@@ -513,11 +533,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                 process_stage(std::integral_constant<bool, true>{}, slot, base, hw, cnt);
             else
                 process_stage(std::integral_constant<bool, false>{}, slot, base, hw, cnt);
-            // the open fibre carries over; fold what the stage closed
             fold();
         }
-        // ---- end of run: close the fibre and the last segment
-        close_fibre();
+        // ---- end of run: the last segment
         fold();
         const bool ends_here = (r1 == p.nnz) || head_at(p, r1);
         emit(first && !head0, !ends_here);
