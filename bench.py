@@ -157,7 +157,7 @@ def barrier(pg):
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("spmttkrp.cu", "internal.cuh"):
+    for f in ("stream_kernel.cuh", "internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1705_09905_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -291,6 +291,19 @@ def bench_spttm(fc, dev, quick):
     byt = ttm_alg_bytes(X, 16, 4)
     return {"workload": cfg.note, "nnz": X.nnz, "nfib": X.nseg, "R": 16, "ms": t * 1e3,
             "alg_bytes": byt, "GBps": byt / t / 1e9, "GFLOPs": 2 * 16 * X.nnz / t / 1e9}
+
+
+def bench_mttkrp_bf16(fc, Xs, dims, R, steps=50):
+    """The same three SpMTTKRP calls with BF16 factors (FP32 accumulation):
+    half the gathered bytes per nonzero."""
+    dev = torch.device("cuda")
+    F = [f.to(dev).to(torch.bfloat16) for f in synth.make_factors(dims, R, seed=1)]
+    outs = [torch.empty((dims[n], R), device=dev) for n in range(3)]
+    total, per_mode = time_spmttkrp(fc, Xs, F, outs, steps, 5, torch.cuda.current_stream())
+    alg = [mttkrp_alg_bytes(Xs[n], R, 2) for n in range(3)]
+    return {"R": R, "factors": "bf16", "ms_per_step": total / steps * 1e3,
+            "GBps": sum(alg) * steps / total / 1e9,
+            "per_mode_ms": [t * 1e3 for t in per_mode]}
 
 
 def bench_cp_als(fc, Xs, dims, sweeps, R=64):
@@ -430,7 +443,8 @@ def run_ours(args):
                                 "sample": f"FP64 C oracle SpMTTKRP, modes 0-2, on the first {nsample} of the "
                                           f"{cfg.nnz} nonzeros (a uniform random subset), {dt:.1f} s"}
     if not args.no_extras and rank == 0:
-        for name, fn in (("spttm", lambda: bench_spttm(fc, dev, args.quick)),
+        for name, fn in (("mttkrp_bf16", lambda: bench_mttkrp_bf16(fc, Xs, cfg.dims, R)),
+                         ("spttm", lambda: bench_spttm(fc, dev, args.quick)),
                          ("cp_als", lambda: bench_cp_als(fc, Xs, cfg.dims, 20 if not args.quick else 5)),
                          ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick))):
             try:

@@ -112,5 +112,10 @@ void stream_params_from(const fcoo_t *X, StreamParams &p);
 // Launch the segmented-reduction kernel for dtype / R (spmttkrp.cu); kind 0
 // weights every nonzero by its value, kind 1 by the residual weight above.
 int launch_stream_kernel(StreamParams &p, int dtype, cudaStream_t s, int kind = 0);
+// The instantiations, one translation unit each (stream_*.cu).
+int launch_stream_f32_k0(StreamParams &p, cudaStream_t s);
+int launch_stream_f32_k1(StreamParams &p, cudaStream_t s);
+int launch_stream_bf16_k0(StreamParams &p, cudaStream_t s);
+int launch_stream_bf16_k1(StreamParams &p, cudaStream_t s);
 
 }  // namespace fcx

@@ -1,0 +1,835 @@
+// stream_kernel.cuh -- the F-COO streaming kernel (templates) shared by the
+// translation units that instantiate it for one factor type and one weight
+// kind each, so that nvcc compiles the variants in parallel.
+// The F-COO streaming kernel behind SpMTTKRP (Eq. 6) and
+// SpTTM (Eq. 3): one-shot product (Sec. IV-C) fused with the segmented
+// reduction over the bit-flags (Sec. IV-D).  The same kernel, with residual
+// weights, computes the sparse CP-fit loss and its adjoint.
+//
+// Work split (GB300 design; the paper's Maxwell layout of one thread per
+// column r and per threadlen partition is replaced):
+//   * a CTA owns a contiguous range of nonzeros (equal count per CTA: the
+//     paper's nnz-balanced partitioning), split into G equal "runs", one per
+//     lane group; a run is a whole number of threadlen partitions, so the
+//     partition's start-flag tells whether the run opens a new segment;
+//   * a lane group of LPR lanes spans the R columns of one output row: each
+//     lane loads E contiguous elements (16 bytes) of every gathered factor row,
+//     so one row gather is a fully coalesced 64..512-byte access;
+//   * the group walks its run in stages of 32 nonzeros.  The index / value
+//     streams and the bit-flag word of a stage are copied by cp.async into a
+//     3-deep ring in shared memory, two stages ahead of use; groups' rings are
+//     offset by 16 bytes modulo 128 so that the 128-bit reads of one warp hit
+//     distinct banks;
+//   * gathers are software-pipelined in quarters of a stage (4 nonzeros, fully
+//     unrolled): the last-product-mode rows of quarter h+1 (and, for 3-way
+//     SpMTTKRP, the rows of the other product mode where a new fibre starts)
+//     are requested before quarter h is consumed, across stage boundaries
+//     too; a row address is one 32x32->64-bit multiply-add;
+//   * the rows of the non-last product modes change only where a new fibre
+//     starts (fixed index mode and non-last product modes): their product brow
+//     is kept in registers and replaced by a predicated select, and each
+//     nonzero adds (val * brow) * row with the paired FP32 instructions
+//     (FMUL2 / FFMA2, two elements per instruction); only quarters that
+//     contain a segment start take a branch;
+//   * every 32 nonzeros the stage sum is folded into the segment sum with
+//     Kahan compensation, so the error of a long (Zipf-hot) segment grows with
+//     its number of stages, not nonzeros;
+//   * a segment that starts and ends inside a run is stored directly (one
+//     plain store per output row); segments cut by run boundaries are combined
+//     per CTA in shared memory (FP64, run order); segments cut by CTA
+//     boundaries leave one FP64 carry per CTA side, and k_carry_fixup adds the
+//     carries of each such segment in CTA order and stores the row.  No
+//     atomics on the output, no pre-zeroing, and the result is bitwise
+//     reproducible for a given handle, R and GPU.
+// The paper replaces atomics with a segmented scan whose inter-block carry is
+// passed by adjacent synchronisation (CTAs spinning on their predecessor); the
+// carry-slot + fixup pass gives the same atomic-free result without any CTA
+// waiting on another.
+#pragma once
+
+#include <limits.h>
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace fcx {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int T = 32;   // nonzeros per stage
+constexpr int NS = 3;   // stages in the ring (two in flight while one is consumed)
+
+// ------------------------------------------------------------ row loads
+
+template <typename TF, int E>
+struct RowIO;
+
+template <>
+struct RowIO<float, 4> {
+    using raw = float4;
+    static __device__ __forceinline__ raw load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+    static __device__ __forceinline__ raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ void cvt(const raw &r, float (&v)[4]) {
+        v[0] = r.x;
+        v[1] = r.y;
+        v[2] = r.z;
+        v[3] = r.w;
+    }
+};
+
+template <>
+struct RowIO<__nv_bfloat16, 8> {
+    using raw = uint4;
+    static __device__ __forceinline__ raw load(const __nv_bfloat16 *p) {
+        return __ldg(reinterpret_cast<const uint4 *>(p));
+    }
+    static __device__ __forceinline__ raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
+    static __device__ __forceinline__ void cvt(const raw &r, float (&v)[8]) {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {  // bf16 -> fp32 is exact: the bits move up 16 places
+            v[2 * i] = __uint_as_float(w[i] << 16);
+            v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+};
+
+template <>
+struct RowIO<float, 1> {
+    using raw = float;
+    static __device__ __forceinline__ raw load(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ raw zero() { return 0.f; }
+    static __device__ __forceinline__ void cvt(const raw &r, float (&v)[1]) { v[0] = r; }
+};
+
+template <>
+struct RowIO<__nv_bfloat16, 1> {
+    using raw = unsigned short;
+    static __device__ __forceinline__ raw load(const __nv_bfloat16 *p) {
+        return __ldg(reinterpret_cast<const unsigned short *>(p));
+    }
+    static __device__ __forceinline__ raw zero() { return 0; }
+    static __device__ __forceinline__ void cvt(const raw &r, float (&v)[1]) { v[0] = __uint_as_float((uint32_t)r << 16); }
+};
+
+template <int E>
+__device__ __forceinline__ void store_row(float *dst, const float (&v)[E]) {
+    if constexpr (E == 4) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (E == 8) {
+        reinterpret_cast<float4 *>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4 *>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) dst[e] = v[e];
+    }
+}
+
+// ------------------------------------------------------------ async copies
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Number of heads (segment starts) strictly before nonzero position pos
+// (pos a multiple of 32): chunk checkpoint plus popcounts of the words since.
+__device__ __forceinline__ int64_t heads_before(const StreamParams &p, int64_t pos, int lig, int lpr,
+                                                unsigned gmask) {
+    int64_t c = pos / kChunk;
+    int64_t w0 = c * (kChunk / 32), w1 = pos >> 5;
+    uint32_t cnt = 0;
+    for (int64_t w = w0 + lig; w < w1; w += lpr) cnt += __popc(__ldg(p.bf + w));
+    for (int o = 1; o < lpr; o <<= 1) cnt += __shfl_xor_sync(gmask, cnt, o);
+    return (int64_t)__ldg(p.hcount + c) + cnt;
+}
+
+__device__ __forceinline__ bool head_at(const StreamParams &p, int64_t pos) {
+    return (__ldg(p.bf + (pos >> 5)) >> (pos & 31)) & 1u;
+}
+
+// Bytes of one stage in the ring (streams + bit-flag word, 16-byte padded)
+// and the per-group ring stride (16 mod 128 so groups hit different banks).
+__host__ __device__ constexpr int slot_bytes(int nstream) { return nstream * T * 4 + 16; }
+__host__ __device__ constexpr int group_stride(int nstream) {
+    return ((NS * slot_bytes(nstream) + 127) / 128) * 128 + 16;
+}
+
+// ------------------------------------------------------------ the kernel
+
+// TF: factor element type; E: elements per lane per chunk (16 bytes for the
+// vector variants); LPR: lanes per group; NCH: column chunks per lane
+// (columns of lane l, chunk c: (c * LPR + l) * E ... + E - 1); NP: number of
+// product modes (0: runtime value p.nprod); KIND: 0 = value weights
+// (SpMTTKRP / SpTTM), 1 = residual weights.
+template <typename TF, int E, int LPR, int NCH, int NP, int KIND>
+__global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
+    using IO = RowIO<TF, E>;
+    using raw = typename IO::raw;
+    constexpr int G = kThreads / LPR;  // groups per CTA
+    constexpr int RT = NCH * LPR * E;  // columns covered by a group
+    const int nprod = NP > 0 ? NP : p.nprod;
+    const int nstream = nprod + 1;
+    const int R = p.R;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int g = tid / LPR, lig = tid % LPR;
+    const unsigned gmask = LPR == 32 ? kFull : (((1u << LPR) - 1u) << (lane / LPR * LPR));
+    const bool has_out = p.out != nullptr;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int sbytes = slot_bytes(nstream);
+    const int gstride = group_stride(nstream);
+    unsigned char *ring = smem + (size_t)g * gstride;
+    double *s_part = reinterpret_cast<double *>(smem + (size_t)G * gstride);
+    int64_t *s_pseg = reinterpret_cast<int64_t *>(s_part + (size_t)2 * G * RT);
+    int *s_pflag = reinterpret_cast<int *>(s_pseg + 2 * G);
+    float *s_loss = reinterpret_cast<float *>(s_pflag + 2 * G);
+    float *s_seg = s_loss + G;  // [G][2][RT] segment sums and compensations
+
+    const int64_t c0 = (int64_t)blockIdx.x * p.cta_chunk;
+    const int64_t c1 = min(c0 + p.cta_chunk, p.nnz);
+    const int64_t r0 = min(c0 + (int64_t)g * p.run_len, c1);
+    const int64_t r1 = min(r0 + p.run_len, c1);
+
+    // columns of this lane
+    int col[NCH];
+    bool act[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        col[c] = (c * LPR + lig) * E;
+        act[c] = col[c] < R;
+    }
+    // loads use a clamped column so that lanes past R read valid memory
+    // unconditionally (their sums are never stored)
+    int colc[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) colc[c] = act[c] ? col[c] : 0;
+    const TF *Fl = static_cast<const TF *>(p.F[nprod - 1]);
+    const TF *Fb = static_cast<const TF *>(p.F[0]);
+
+    if (lig == 0) {
+        s_pseg[2 * g] = -1;
+        s_pseg[2 * g + 1] = -1;
+        s_pflag[2 * g] = 0;
+        s_pflag[2 * g + 1] = 0;
+        s_loss[g] = 0.f;
+    }
+    if (tid == 0 && has_out) {
+        p.carry_seg[2 * blockIdx.x] = -1;
+        p.carry_seg[2 * blockIdx.x + 1] = -1;
+    }
+
+    if (r0 < r1) {
+        const int nst = (int)((r1 - r0 + T - 1) / T);
+        // ---- stream prefetch: stage s -> ring slot s % NS
+        auto issue_stage = [&](int s) {
+            if (s < nst) {
+                const int64_t base = r0 + (int64_t)s * T;
+                unsigned char *slot = ring + (s % NS) * sbytes;
+                const int nchunks = nstream * (T / 4);
+                for (int c = lig; c < nchunks; c += LPR) {
+                    const int a = c / (T / 4), q = c % (T / 4);
+                    const void *src = a < nprod ? (const void *)(p.pidx[a] + base + q * 4)
+                                                : (const void *)(p.val + base + q * 4);
+                    cp_async16(slot + a * T * 4 + q * 16, src);
+                }
+                if (lig == 0) cp_async4(slot + nstream * T * 4, p.bf + (base >> 5));
+            }
+            cp_async_commit();
+        };
+#pragma unroll
+        for (int s = 0; s < NS - 1; ++s) issue_stage(s);
+
+        // segment containing r0 and whether r0 opens it (start-flag of the partition)
+        const int64_t part = r0 / p.threadlen;
+        const bool head0 = (__ldg(p.sf + (part >> 5)) >> (part & 31)) & 1u;
+        int64_t seg = heads_before(p, r0, lig, LPR, gmask) + (head0 ? 1 : 0) - 1;
+        int64_t row = p.segrow ? (int64_t)__ldg(p.segrow + seg) : seg;
+        bool first = true;  // the current segment is the run's first
+        float lsum = 0.f;
+
+        // rows between the previous segment's row and this one hold no nonzeros
+        auto fill_gap = [&](int64_t from, int64_t to) {  // rows from+1 .. to-1
+            for (int64_t rr = from + 1; rr < to; ++rr) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    if (act[c]) {
+                        float z[E];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) z[e] = 0.f;
+                        store_row<E>(p.out + rr * R + col[c], z);
+                    }
+            }
+        };
+        if (has_out && p.segrow && head0) fill_gap(seg > 0 ? (int64_t)__ldg(p.segrow + seg - 1) : -1, row);
+
+        // accumulators: the stage sum in registers; once a segment reaches the
+        // end of a stage, its running sum and Kahan compensation move to
+        // shared memory (folded once per stage); a segment that starts and
+        // ends between two folds never leaves registers.  brow = product of
+        // the current fibre's non-last product-mode rows
+        float acc_st[NCH][E], brow[NCH][E];
+        float trow[KIND == 1 ? NCH : 1][E];
+        float *s_acc = s_seg + (size_t)g * 2 * RT;  // [RT] sum, then [RT] compensation
+        float *s_cmp = s_acc + RT;
+        bool in_smem = false;  // the current segment has a folded part in s_acc / s_cmp
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                acc_st[c][e] = 0.f;
+                brow[c][e] = 1.f;
+            }
+        auto load_target = [&]() {
+            if constexpr (KIND == 1) {
+                const TF *Tm = static_cast<const TF *>(p.T);
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    if (act[c]) {
+                        IO::cvt(IO::load(Tm + (size_t)row * R + col[c]), trow[c]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) trow[c][e] = 0.f;  // masks the clamped lanes
+                    }
+                }
+            }
+        };
+        load_target();
+
+        auto fold = [&]() {  // Kahan: segment sum += acc_st
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if (in_smem) {
+                        const float a = s_acc[col[c] + e];
+                        const float y = acc_st[c][e] - s_cmp[col[c] + e];
+                        const float t = a + y;
+                        s_cmp[col[c] + e] = (t - a) - y;
+                        s_acc[col[c] + e] = t;
+                    } else {
+                        s_acc[col[c] + e] = acc_st[c][e];
+                        s_cmp[col[c] + e] = 0.f;
+                    }
+                    acc_st[c][e] = 0.f;
+                }
+            in_smem = true;
+        };
+        // the finished segment's value, element e of chunk c
+        auto seg_value = [&](int c, int e) -> double {
+            return in_smem ? (double)s_acc[col[c] + e] - (double)s_cmp[col[c] + e] : (double)acc_st[c][e];
+        };
+        // hand a finished (or run-cut) segment to its writer
+        auto emit = [&](bool starts_before, bool continues_after) {
+            if (!has_out) return;
+            if (in_smem) fold();
+            if (!starts_before && !continues_after) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    if (act[c]) {
+                        float v[E];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) v[e] = (float)seg_value(c, e);
+                        store_row<E>(p.out + row * R + col[c], v);
+                    }
+            } else {
+                const int slot = 2 * g + (first ? 0 : 1);
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) s_part[(size_t)slot * RT + col[c] + e] = seg_value(c, e);
+                if (lig == 0) {
+                    s_pseg[slot] = seg;
+                    s_pflag[slot] = (starts_before ? 1 : 0) | (continues_after ? 2 : 0);
+                }
+            }
+        };
+        // a new segment starts at this nonzero
+        auto new_segment = [&]() {
+            emit(first && !head0, false);
+            first = false;
+            in_smem = false;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc_st[c][e] = 0.f;
+            const int64_t prev = row;
+            ++seg;
+            row = p.segrow ? (int64_t)__ldg(p.segrow + seg) : seg;
+            if (has_out && p.segrow) fill_gap(prev, row);
+            load_target();
+        };
+        // acc_st += w * (brow * row), w = val (KIND 0) or the residual weight
+        // (KIND 1); element pairs go through the paired FP32 instructions
+        auto accumulate = [&](float v, const raw (&cr)[NCH], int64_t pos) {
+            float t[NCH][E];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) IO::cvt(cr[c], t[c]);
+            if constexpr (KIND == 0) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    if constexpr (E % 2 == 0) {
+                        const float2 v2 = make_float2(v, v);
+#pragma unroll
+                        for (int e = 0; e < E; e += 2) {
+                            const float2 s = __fmul2_rn(v2, make_float2(brow[c][e], brow[c][e + 1]));
+                            const float2 a = __ffma2_rn(s, make_float2(t[c][e], t[c][e + 1]),
+                                                        make_float2(acc_st[c][e], acc_st[c][e + 1]));
+                            acc_st[c][e] = a.x;
+                            acc_st[c][e + 1] = a.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) acc_st[c][e] = fmaf(v * brow[c][e], t[c][e], acc_st[c][e]);
+                    }
+                }
+            } else {
+                // h = brow * row; e = <T(row), h> - val; acc_st += e * h
+                float h[NCH][E];
+                float d = 0.f;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        h[c][e] = brow[c][e] * t[c][e];
+                        d = fmaf(trow[c][e], h[c][e], d);
+                    }
+#pragma unroll
+                for (int o = 1; o < LPR; o <<= 1) d += __shfl_xor_sync(gmask, d, o);
+                const float w = p.sub_val ? d - v : d;
+                if (lig == 0) {
+                    lsum = fmaf(w, w, lsum);
+                    if (p.dvals) p.dvals[__ldg(p.perm + pos)] = p.dsign * w;
+                }
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+#pragma unroll
+                    for (int e = 0; e < E; ++e) acc_st[c][e] = fmaf(w, h[c][e], acc_st[c][e]);
+            }
+        };
+        // brow from the rows of the non-last product modes (general N)
+        auto set_brow_sync = [&](const unsigned char *slot, int u) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) brow[c][e] = 1.f;
+                for (int m = 0; m < nprod - 1; ++m) {
+                    const TF *Fm = static_cast<const TF *>(p.F[m]);
+                    const uint32_t km = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[u];
+                    float t[E];
+                    IO::cvt(IO::load(Fm + (size_t)km * R + colc[c]), t);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) brow[c][e] *= t[e];
+                }
+            }
+        };
+
+        uint32_t jprev = 0xffffffffu;           // fibre key of the previous nonzero (3-way)
+        uint32_t lastkey[FCOO_MAX_MODES - 1];  // fibre keys of the previous nonzero (general)
+#pragma unroll
+        for (int m = 0; m < FCOO_MAX_MODES - 1; ++m) lastkey[m] = 0xffffffffu;
+
+        // Row addresses: one 32 x 32 -> 64-bit multiply-add from a per-lane base.
+        const uint32_t Rb = (uint32_t)R * (uint32_t)sizeof(TF);
+        const char *Flb[NCH];
+        const char *Fbb[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            Flb[c] = reinterpret_cast<const char *>(Fl + colc[c]);
+            Fbb[c] = reinterpret_cast<const char *>(Fb + colc[c]);
+        }
+
+        // ---- software pipeline over quarters of a stage (Q nonzeros; 4, or 2
+        // when a lane holds more than 4 columns): the gathers of quarter h+1
+        // are in flight while quarter h is consumed.  Full stages are unrolled
+        // (static offsets and masks); the first quarter of the next stage is
+        // requested while the last quarter of the current one is consumed.
+        constexpr int Q = E * NCH <= 4 ? 4 : 2;
+        constexpr int QPS = T / Q;  // quarters per stage
+        // the unrolled pipeline serves the 3-way SpMTTKRP and SpTTM vector
+        // variants; the general-N and scalar ones walk nonzeros one at a time
+        constexpr bool PIPE = (NP == 1 || NP == 2) && E > 1;
+        struct Quarter {
+            raw cr[Q][NCH];
+            raw br[NP == 2 ? Q : 1][NCH];
+            float vv[Q];
+            uint32_t fcm;
+        };
+        // read quarter qt of a full stage from its slot and start its gathers;
+        // hw = the stage's segment-start bits
+        auto prefetch = [&](Quarter &b, const unsigned char *slot, int qt, uint32_t hw) {
+            const int ub = qt * Q;
+            uint32_t kk[Q], jj[Q];
+            if constexpr (Q == 4) {
+                const uint4 k4 = *reinterpret_cast<const uint4 *>(slot + (nprod - 1) * T * 4 + ub * 4);
+                const float4 v4 = *reinterpret_cast<const float4 *>(slot + nprod * T * 4 + ub * 4);
+                kk[0] = k4.x, kk[1] = k4.y, kk[2] = k4.z, kk[3] = k4.w;
+                b.vv[0] = v4.x, b.vv[1] = v4.y, b.vv[2] = v4.z, b.vv[3] = v4.w;
+            } else {
+                const uint2 k2 = *reinterpret_cast<const uint2 *>(slot + (nprod - 1) * T * 4 + ub * 4);
+                const float2 v2 = *reinterpret_cast<const float2 *>(slot + nprod * T * 4 + ub * 4);
+                kk[0] = k2.x, kk[1] = k2.y;
+                b.vv[0] = v2.x, b.vv[1] = v2.y;
+            }
+            uint32_t fcm = (hw >> ub) & ((1u << Q) - 1u);
+            if constexpr (NP == 2) {
+                if constexpr (Q == 4) {
+                    const uint4 j4 = *reinterpret_cast<const uint4 *>(slot + ub * 4);
+                    jj[0] = j4.x, jj[1] = j4.y, jj[2] = j4.z, jj[3] = j4.w;
+                } else {
+                    const uint2 j2 = *reinterpret_cast<const uint2 *>(slot + ub * 4);
+                    jj[0] = j2.x, jj[1] = j2.y;
+                }
+#pragma unroll
+                for (int q = 0; q < Q; ++q) fcm |= (uint32_t)(jj[q] != (q ? jj[q - 1] : jprev)) << q;
+                jprev = jj[Q - 1];
+            } else if constexpr (NP != 1) {
+                for (int q = 0; q < Q; ++q) {
+                    bool ch = false;
+                    for (int m = 0; m < nprod - 1; ++m) {
+                        const uint32_t k = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[ub + q];
+                        ch |= k != lastkey[m];
+                        lastkey[m] = k;
+                    }
+                    fcm |= (uint32_t)ch << q;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    b.cr[q][c] = IO::load(reinterpret_cast<const TF *>(Flb[c] + (uint64_t)kk[q] * Rb));
+                if constexpr (NP == 2) {
+                    const bool f = (fcm >> q) & 1u;
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c)
+                        b.br[q][c] = f ? IO::load(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)jj[q] * Rb))
+                                       : IO::zero();
+                }
+            }
+            b.fcm = fcm;
+        };
+        // consume quarter qt (hdm = its segment-start bits)
+        auto consume = [&](const Quarter &b, const unsigned char *slot, int qt, uint32_t hdm, int64_t base) {
+            if (hdm == 0) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const bool f = (b.fcm >> q) & 1u;
+                    if constexpr (NP == 2) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) {
+                            float t[E];
+                            IO::cvt(b.br[q][c], t);
+#pragma unroll
+                            for (int e = 0; e < E; ++e) brow[c][e] = f ? t[e] : brow[c][e];
+                        }
+                    } else if constexpr (NP != 1) {
+                        if (f) set_brow_sync(slot, qt * Q + q);
+                    }
+                    accumulate(b.vv[q], b.cr[q], base + qt * Q + q);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    if ((hdm >> q) & 1u) new_segment();
+                    if ((b.fcm >> q) & 1u) {
+                        if constexpr (NP == 2) {
+#pragma unroll
+                            for (int c = 0; c < NCH; ++c) IO::cvt(b.br[q][c], brow[c]);
+                        } else if constexpr (NP != 1) {
+                            set_brow_sync(slot, qt * Q + q);
+                        }
+                    }
+                    accumulate(b.vv[q], b.cr[q], base + qt * Q + q);
+                }
+            }
+        };
+        // ragged last stage: nonzeros one at a time, no pipelining
+        auto process_tail = [&](const unsigned char *slot, int64_t base, uint32_t hw, int cnt) {
+            const uint32_t *sk = reinterpret_cast<const uint32_t *>(slot + (nprod - 1) * T * 4);
+            const uint32_t *sj = reinterpret_cast<const uint32_t *>(slot);
+            const float *sv = reinterpret_cast<const float *>(slot + nprod * T * 4);
+            for (int u = 0; u < cnt; ++u) {
+                const bool hd = (hw >> u) & 1u;
+                bool f = hd;
+                if constexpr (NP == 2) {
+                    f |= sj[u] != jprev;
+                    jprev = sj[u];
+                } else if constexpr (NP != 1) {
+                    for (int m = 0; m < nprod - 1; ++m) {
+                        const uint32_t k = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[u];
+                        f |= k != lastkey[m];
+                        lastkey[m] = k;
+                    }
+                }
+                raw cr[NCH];
+#pragma unroll
+                for (int c = 0; c < NCH; ++c)
+                    cr[c] = IO::load(reinterpret_cast<const TF *>(Flb[c] + (uint64_t)sk[u] * Rb));
+                if (hd) new_segment();
+                if (f) {
+                    if constexpr (NP == 2) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c)
+                            IO::cvt(IO::load(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sj[u] * Rb)), brow[c]);
+                    } else if constexpr (NP != 1) {
+                        set_brow_sync(slot, u);
+                    }
+                }
+                accumulate(sv[u], cr, base + u);
+            }
+        };
+
+        Quarter qa, qb;
+        bool have_first = false;  // qa already holds quarter 0 of the current stage
+#pragma unroll 1
+        for (int s = 0; s < nst; ++s) {
+            __syncwarp(gmask);  // the previous stage's slot is no longer read
+            issue_stage(s + NS - 1);
+            cp_async_wait<NS - 1>();
+            __syncwarp(gmask);
+            const unsigned char *slot = ring + (s % NS) * sbytes;
+            const int64_t base = r0 + (int64_t)s * T;
+            const int cnt = (int)min((int64_t)T, r1 - base);
+            uint32_t hw = *reinterpret_cast<const uint32_t *>(slot + nstream * T * 4);
+            if (s == 0) hw &= ~1u;  // r0 opens the run, not a new segment
+            if (PIPE && cnt == T) {
+                if (!have_first) prefetch(qa, slot, 0, hw);
+                have_first = false;
+#pragma unroll
+                for (int qt = 0; qt < QPS; ++qt) {
+                    Quarter &cur = (qt & 1) ? qb : qa;
+                    Quarter &nxt = (qt & 1) ? qa : qb;
+                    if (qt + 1 < QPS) {
+                        prefetch(nxt, slot, qt + 1, hw);
+                    } else if (s + 1 < nst && r1 - (base + T) >= T) {
+                        // the next stage is full: request its first quarter now
+                        cp_async_wait<NS - 2>();
+                        __syncwarp(gmask);
+                        const unsigned char *nslot = ring + ((s + 1) % NS) * sbytes;
+                        prefetch(nxt, nslot, 0, *reinterpret_cast<const uint32_t *>(nslot + nstream * T * 4));
+                        have_first = true;
+                    }
+                    consume(cur, slot, qt, (hw >> (qt * Q)) & ((1u << Q) - 1u), base);
+                }
+            } else {
+                process_tail(slot, base, hw, cnt);
+            }
+            fold();  // stage sums folded every 32 nonzeros
+        }
+        // ---- end of run: the last segment
+        const bool ends_here = (r1 == p.nnz) || head_at(p, r1);
+        emit(first && !head0, !ends_here);
+        if (has_out && p.segrow && r1 == p.nnz) fill_gap(row, p.out_rows);
+        if (KIND == 1 && lig == 0) s_loss[g] = lsum;
+    }
+
+    __syncthreads();
+    if (KIND == 1 && p.loss_part) {
+        if (tid == 0) {
+            double s = 0.0;
+            for (int q = 0; q < G; ++q) s += (double)s_loss[q];
+            p.loss_part[blockIdx.x] = s;
+        }
+    }
+    if (!has_out) return;
+    // ---- combine the run-cut segments of this CTA in run order (FP64)
+    const int last_group = (int)min((int64_t)G - 1, (c1 - c0 + p.run_len - 1) / p.run_len - 1);
+    for (int t = tid; t < R; t += kThreads) {
+        int64_t cur = -1;
+        double sum = 0.0;
+        int cur_first_e = -1, cur_last_e = -1;
+        auto flush = [&]() {
+            if (cur < 0) return;
+            const bool before = cur_first_e / 2 == 0 && (s_pflag[cur_first_e] & 1);
+            const bool after = cur_last_e / 2 == last_group && (s_pflag[cur_last_e] & 2);
+            if (before || after) {
+                const int64_t slot = 2 * (int64_t)blockIdx.x + (before ? 0 : 1);
+                p.carry_val[slot * R + t] = sum;
+                if (t == 0) p.carry_seg[slot] = (cur << 2) | (before ? 1 : 0) | (after ? 2 : 0);
+            } else {
+                const int64_t orow = p.segrow ? (int64_t)__ldg(p.segrow + cur) : cur;
+                p.out[orow * R + t] = (float)sum;
+            }
+        };
+        for (int e = 0; e < 2 * G; ++e) {
+            const int64_t sg = s_pseg[e];
+            if (sg < 0) continue;
+            if (sg != cur) {
+                flush();
+                cur = sg;
+                sum = 0.0;
+                cur_first_e = e;
+            }
+            cur_last_e = e;
+            sum += s_part[(size_t)e * RT + t];
+        }
+        flush();
+    }
+}
+
+// One block per CTA boundary b (between CTAs b-1 and b).  If a segment crosses
+// b and b is the first boundary it crosses, this block adds its carries -- CTA
+// b-1's, then CTA b, b+1, ... up to the CTA where it ends -- in CTA order and
+// stores the output row.
+__global__ void __launch_bounds__(256) k_carry_fixup(const StreamParams p) {
+    const int b = blockIdx.x + 1;
+    if (b >= p.grid) return;
+    const int64_t e1 = p.carry_seg[2 * (b - 1) + 1], e0 = p.carry_seg[2 * (b - 1)];
+    int aslot;
+    int64_t a;
+    if (e1 >= 0 && (e1 & 2)) {
+        a = e1;
+        aslot = 1;
+    } else if (e0 >= 0 && (e0 & 2)) {
+        a = e0;
+        aslot = 0;
+    } else {
+        return;  // boundary b cuts no segment
+    }
+    if (a & 1) return;  // the segment started before CTA b-1: an earlier block owns it
+    const int64_t seg = a >> 2;
+    __shared__ int s_end;
+    if (threadIdx.x == 0) s_end = INT_MAX;
+    __syncthreads();
+    for (int base = b; base < p.grid; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        if (j < p.grid) {
+            const int64_t c = p.carry_seg[2 * (int64_t)j];
+            if (c < 0 || !(c & 2)) atomicMin(&s_end, j);
+        }
+        __syncthreads();
+        const bool done = s_end != INT_MAX;
+        __syncthreads();
+        if (done) break;
+    }
+    const int end = min(s_end, p.grid - 1);
+    const int count = end - b + 2;  // (b-1, aslot) then (j, 0) for j = b..end
+    const int nw = blockDim.x / 32, w = threadIdx.x / 32, lane = threadIdx.x & 31;
+    const int R = p.R;
+    double acc[FCOO_MAX_RANK / 32];
+#pragma unroll
+    for (int i = 0; i < FCOO_MAX_RANK / 32; ++i) acc[i] = 0.0;
+    for (int k = w; k < count; k += nw) {
+        const int64_t slot = k == 0 ? 2 * (int64_t)(b - 1) + aslot : 2 * (int64_t)(b + k - 1);
+#pragma unroll
+        for (int i = 0; i < FCOO_MAX_RANK / 32; ++i) {
+            const int t = lane + 32 * i;
+            if (t < R) acc[i] += __ldcg(p.carry_val + slot * R + t);
+        }
+    }
+    __shared__ double s_w[8][FCOO_MAX_RANK];
+#pragma unroll
+    for (int i = 0; i < FCOO_MAX_RANK / 32; ++i) {
+        const int t = lane + 32 * i;
+        if (t < R) s_w[w][t] = acc[i];
+    }
+    __syncthreads();
+    const int64_t row = p.segrow ? (int64_t)__ldg(p.segrow + seg) : seg;
+    for (int t = threadIdx.x; t < R; t += blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < nw; ++q) s += s_w[q][t];
+        p.out[row * R + t] = (float)s;
+    }
+}
+
+// ------------------------------------------------------------ launch
+
+int g_sms = 0;
+int sms() {
+    if (!g_sms) g_sms = num_sms();
+    return g_sms;
+}
+
+template <typename TF, int E, int LPR, int NCH, int NP, int KIND>
+int launch_variant(StreamParams &p, cudaStream_t s) {
+    constexpr int G = kThreads / LPR;
+    constexpr int RT = NCH * LPR * E;
+    auto kern = k_stream<TF, E, LPR, NCH, NP, KIND>;
+    const size_t smem = (size_t)G * group_stride(p.nprod + 1) + (size_t)2 * G * RT * 8 + (size_t)2 * G * 8 +
+                        (size_t)2 * G * 4 + (size_t)G * 4 + (size_t)G * 2 * RT * 4;
+    static size_t cached_smem = 0;
+    static int cached_occ = 0;
+    if (cached_smem != smem) {
+        FCOO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int occ = 0;
+        FCOO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+        if (occ < 1) return fail(FCOO_ERR_UNSUPPORTED, "stream kernel does not fit on an SM (smem %zu)", smem);
+        cached_occ = occ;
+        cached_smem = smem;
+    }
+    const int64_t ra = p.threadlen > 32 ? p.threadlen : 32;
+    const int64_t max_ctas = std::min<int64_t>((int64_t)sms() * cached_occ, p.grid);
+    int64_t grid = std::min<int64_t>(max_ctas, ceil_div(p.nnz, (int64_t)G * ra));
+    if (grid < 1) grid = 1;
+    p.run_len = round_up(ceil_div(p.nnz, grid * G), ra);
+    p.cta_chunk = p.run_len * G;
+    grid = ceil_div(p.nnz, p.cta_chunk);
+    p.grid = (int)grid;
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(p);
+    FCOO_CUDA(cudaGetLastError());
+    if (p.out && grid > 1) {
+        k_carry_fixup<<<(unsigned)(grid - 1), 256, 0, s>>>(p);
+        FCOO_CUDA(cudaGetLastError());
+    }
+    return FCOO_OK;
+}
+
+template <typename TF, int E, int LPR, int NCH, int KIND>
+int launch_np(StreamParams &p, cudaStream_t s) {
+    switch (p.nprod) {
+        case 1:
+            if constexpr (KIND == 0) return launch_variant<TF, E, LPR, NCH, 1, KIND>(p, s);
+            return launch_variant<TF, E, LPR, NCH, 0, KIND>(p, s);
+        case 2: return launch_variant<TF, E, LPR, NCH, 2, KIND>(p, s);
+        default: return launch_variant<TF, E, LPR, NCH, 0, KIND>(p, s);
+    }
+}
+
+// 16-byte lanes: E = 16 / sizeof(TF) elements each
+template <typename TF, int E, int KIND>
+int launch_vec(StreamParams &p, cudaStream_t s) {
+    const int chunks = p.R / E;
+    if (chunks <= 4) return launch_np<TF, E, 4, 1, KIND>(p, s);
+    if (chunks <= 8) return launch_np<TF, E, 8, 1, KIND>(p, s);
+    if (chunks <= 16) return launch_np<TF, E, 16, 1, KIND>(p, s);
+    if (chunks <= 32) return launch_np<TF, E, 32, 1, KIND>(p, s);
+    if constexpr (E == 4) return launch_np<TF, E, 32, 2, KIND>(p, s);
+    return fail(FCOO_ERR_UNSUPPORTED, "R=%d above the supported rank", p.R);
+}
+
+// scalar lanes for ranks that are not a multiple of the vector width
+template <typename TF, int KIND>
+int launch_scalar(StreamParams &p, cudaStream_t s) {
+    const int nch = (p.R + 31) / 32;
+    if (nch <= 1) return launch_variant<TF, 1, 32, 1, 0, KIND>(p, s);
+    if (nch <= 2) return launch_variant<TF, 1, 32, 2, 0, KIND>(p, s);
+    if (nch <= 4) return launch_variant<TF, 1, 32, 4, 0, KIND>(p, s);
+    return launch_variant<TF, 1, 32, 8, 0, KIND>(p, s);
+}
+
+bool aligned16(const void *q) { return q == nullptr || ((uintptr_t)q & 15u) == 0; }
+
+// 16-byte lanes when R is a multiple of the vector width and every row
+// pointer is 16-byte aligned, scalar lanes otherwise.
+template <typename TF, int E, int KIND>
+int launch_typed(StreamParams &p, cudaStream_t s) {
+    bool vec = p.R % E == 0 && aligned16(p.out) && aligned16(p.T);
+    for (int m = 0; m < p.nprod; ++m) vec = vec && aligned16(p.F[m]);
+    return vec ? launch_vec<TF, E, KIND>(p, s) : launch_scalar<TF, KIND>(p, s);
+}
+
+}  // namespace
+}  // namespace fcx
