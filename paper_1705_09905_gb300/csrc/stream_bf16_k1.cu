@@ -4,7 +4,7 @@
 namespace fcx {
 
 int launch_stream_bf16_k1(StreamParams &p, cudaStream_t s) {
-    return launch_typed<__nv_bfloat16, 8, 1>(p, s);
+    return launch_typed<__nv_bfloat16, 1>(p, s);
 }
 
 }  // namespace fcx

@@ -4,7 +4,7 @@
 namespace fcx {
 
 int launch_stream_f32_k0(StreamParams &p, cudaStream_t s) {
-    return launch_typed<float, 4, 0>(p, s);
+    return launch_typed<float, 0>(p, s);
 }
 
 }  // namespace fcx

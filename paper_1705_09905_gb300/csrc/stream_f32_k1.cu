@@ -4,7 +4,7 @@
 namespace fcx {
 
 int launch_stream_f32_k1(StreamParams &p, cudaStream_t s) {
-    return launch_typed<float, 4, 1>(p, s);
+    return launch_typed<float, 1>(p, s);
 }
 
 }  // namespace fcx

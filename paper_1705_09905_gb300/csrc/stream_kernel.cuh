@@ -60,7 +60,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int T = 32;   // nonzeros per stage
-constexpr int NS = 3;   // stages in the ring (two in flight while one is consumed)
+constexpr int NS = 2;   // stages in the ring (one in flight while one is consumed)
 
 // ------------------------------------------------------------ row loads
 
@@ -72,11 +72,50 @@ struct RowIO<float, 4> {
     using raw = float4;
     static __device__ __forceinline__ raw load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
     static __device__ __forceinline__ raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ raw load_if(const float *p, bool f) { return f ? load(p) : zero(); }
     static __device__ __forceinline__ void cvt(const raw &r, float (&v)[4]) {
         v[0] = r.x;
         v[1] = r.y;
         v[2] = r.z;
         v[3] = r.w;
+    }
+};
+
+// 32-byte lanes: one 256-bit load per lane and row (eight FP32 columns)
+struct F8 {
+    float v[8];
+};
+template <>
+struct RowIO<float, 8> {
+    using raw = F8;
+    static __device__ __forceinline__ raw load(const float *p) {
+        raw r;
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+              "=f"(r.v[7])
+            : "l"(p));
+        return r;
+    }
+    static __device__ __forceinline__ raw zero() {
+        raw r;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r.v[i] = 0.f;
+        return r;
+    }
+    // the load only where f holds (zeros elsewhere), as one predicated instruction
+    static __device__ __forceinline__ raw load_if(const float *p, bool f) {
+        raw r = zero();
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %9, 0;\n\t"
+            "@q ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t}"
+            : "+f"(r.v[0]), "+f"(r.v[1]), "+f"(r.v[2]), "+f"(r.v[3]), "+f"(r.v[4]), "+f"(r.v[5]), "+f"(r.v[6]),
+              "+f"(r.v[7])
+            : "l"(p), "r"((unsigned)f));
+        return r;
+    }
+    static __device__ __forceinline__ void cvt(const raw &r, float (&v)[8]) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = r.v[i];
     }
 };
 
@@ -87,6 +126,7 @@ struct RowIO<__nv_bfloat16, 8> {
         return __ldg(reinterpret_cast<const uint4 *>(p));
     }
     static __device__ __forceinline__ raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
+    static __device__ __forceinline__ raw load_if(const __nv_bfloat16 *p, bool f) { return f ? load(p) : zero(); }
     static __device__ __forceinline__ void cvt(const raw &r, float (&v)[8]) {
         const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
@@ -102,6 +142,7 @@ struct RowIO<float, 1> {
     using raw = float;
     static __device__ __forceinline__ raw load(const float *p) { return __ldg(p); }
     static __device__ __forceinline__ raw zero() { return 0.f; }
+    static __device__ __forceinline__ raw load_if(const float *p, bool f) { return f ? load(p) : zero(); }
     static __device__ __forceinline__ void cvt(const raw &r, float (&v)[1]) { v[0] = r; }
 };
 
@@ -112,6 +153,7 @@ struct RowIO<__nv_bfloat16, 1> {
         return __ldg(reinterpret_cast<const unsigned short *>(p));
     }
     static __device__ __forceinline__ raw zero() { return 0; }
+    static __device__ __forceinline__ raw load_if(const __nv_bfloat16 *p, bool f) { return f ? load(p) : zero(); }
     static __device__ __forceinline__ void cvt(const raw &r, float (&v)[1]) { v[0] = __uint_as_float((uint32_t)r << 16); }
 };
 
@@ -161,10 +203,87 @@ __device__ __forceinline__ bool head_at(const StreamParams &p, int64_t pos) {
 }
 
 // Bytes of one stage in the ring (streams + bit-flag word, 16-byte padded)
-// and the per-group ring stride (16 mod 128 so groups hit different banks).
+// and the per-group region stride (16 mod 128 so groups hit different banks).
+// After its run a group reuses its region for the FP64 partial of its last
+// segment (rt columns), so the region holds whichever is larger.
 __host__ __device__ constexpr int slot_bytes(int nstream) { return nstream * T * 4 + 16; }
-__host__ __device__ constexpr int group_stride(int nstream) {
-    return ((NS * slot_bytes(nstream) + 127) / 128) * 128 + 16;
+__host__ __device__ constexpr int group_stride(int nstream, int rt) {
+    return (((NS * slot_bytes(nstream) > rt * 8 ? NS * slot_bytes(nstream) : rt * 8) + 127) / 128) * 128 + 16;
+}
+// Bytes of dynamic shared memory of one CTA of the streaming kernel.
+__host__ __device__ constexpr size_t stream_smem_bytes(int nstream, int G, int RT) {
+    return (size_t)G * group_stride(nstream, RT)  // stream rings / last-segment partials
+           + (size_t)G * RT * 8                   // first-segment partials (FP64)
+           + (size_t)2 * G * 8 + (size_t)2 * G * 4 + (size_t)G * 4  // segment ids, flags, loss
+           + (size_t)G * 2 * RT * 4;              // Kahan sums and compensations
+}
+
+// ------------------------------------------------------------ segment output
+
+// Float offset of element e of column chunk c of lane lig in a group's Kahan
+// sum / compensation arrays: the 16-byte pieces of the lanes of a warp are
+// contiguous, so 128-bit accesses are conflict-free.
+template <int E, int LPR>
+__device__ __forceinline__ int acc_slot(int c, int e, int lig) {
+    if constexpr (E % 4 == 0)
+        return ((c * (E / 4) + e / 4) * LPR + lig) * 4 + e % 4;
+    else
+        return (c * LPR + lig) * E + e;
+}
+
+template <int E, int NCH>
+struct SegAcc {
+    float v[NCH][E];
+};
+
+// A finished segment that reached a fold or was cut by the run: its value is
+// the stage sum a plus, when in_smem, the Kahan sum minus its compensation.
+// Written to the output row orow (part == NULL, FP32) or to the FP64 partial
+// part[] of the CTA combine.  It runs once per run or per long segment; the
+// out-of-line copies below keep the loop of the short-segment variants small.
+template <int E, int NCH, int LPR>
+__device__ __forceinline__ void emit_segment_body(const SegAcc<E, NCH> &a, bool in_smem, const float *s_acc,
+                                                  const float *s_cmp, int lig, int R, float *orow, double *part) {
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const int col = (c * LPR + lig) * E;
+        if (part) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = acc_slot<E, LPR>(c, e, lig);
+                part[col + e] = in_smem ? (double)s_acc[i] + ((double)a.v[c][e] - (double)s_cmp[i]) : (double)a.v[c][e];
+            }
+        } else if (col < R) {
+            float v[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = acc_slot<E, LPR>(c, e, lig);
+                v[e] = in_smem ? s_acc[i] + (a.v[c][e] - s_cmp[i]) : a.v[c][e];
+            }
+            store_row<E>(orow + col, v);
+        }
+    }
+}
+
+template <int E, int NCH, int LPR>
+__device__ __noinline__ void emit_segment_outlined(SegAcc<E, NCH> a, bool in_smem, const float *s_acc,
+                                                   const float *s_cmp, int lig, int R, float *orow, double *part) {
+    emit_segment_body<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, R, orow, part);
+}
+
+// Rows from+1 .. to-1 of out hold no nonzeros: zero this lane's columns.
+template <int E, int NCH, int LPR>
+__device__ __forceinline__ void zero_rows(float *out, int R, int lig, int64_t from, int64_t to) {
+    float z[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) z[e] = 0.f;
+    for (int64_t rr = from + 1; rr < to; ++rr) {
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            const int col = (c * LPR + lig) * E;
+            if (col < R) store_row<E>(out + rr * R + col, z);
+        }
+    }
 }
 
 // ------------------------------------------------------------ the kernel
@@ -190,13 +309,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
 
     extern __shared__ __align__(128) unsigned char smem[];
     const int sbytes = slot_bytes(nstream);
-    const int gstride = group_stride(nstream);
+    const int gstride = group_stride(nstream, RT);
     unsigned char *ring = smem + (size_t)g * gstride;
-    double *s_part = reinterpret_cast<double *>(smem + (size_t)G * gstride);
-    int64_t *s_pseg = reinterpret_cast<int64_t *>(s_part + (size_t)2 * G * RT);
+    double *s_first = reinterpret_cast<double *>(smem + (size_t)G * gstride);  // [G][RT]
+    int64_t *s_pseg = reinterpret_cast<int64_t *>(s_first + (size_t)G * RT);
     int *s_pflag = reinterpret_cast<int *>(s_pseg + 2 * G);
     float *s_loss = reinterpret_cast<float *>(s_pflag + 2 * G);
     float *s_seg = s_loss + G;  // [G][2][RT] segment sums and compensations
+    // partial of run-cut segment e (slot 2g: the run's first segment, 2g+1:
+    // its last, kept in the group's region once the run is done)
+    auto part_ptr = [&](int e) -> double * {
+        return (e & 1) ? reinterpret_cast<double *>(smem + (size_t)(e >> 1) * gstride)
+                       : s_first + (size_t)(e >> 1) * RT;
+    };
 
     const int64_t c0 = (int64_t)blockIdx.x * p.cta_chunk;
     const int64_t c1 = min(c0 + p.cta_chunk, p.nnz);
@@ -238,12 +363,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
             if (s < nst) {
                 const int64_t base = r0 + (int64_t)s * T;
                 unsigned char *slot = ring + (s % NS) * sbytes;
-                const int nchunks = nstream * (T / 4);
-                for (int c = lig; c < nchunks; c += LPR) {
-                    const int a = c / (T / 4), q = c % (T / 4);
-                    const void *src = a < nprod ? (const void *)(p.pidx[a] + base + q * 4)
-                                                : (const void *)(p.val + base + q * 4);
-                    cp_async16(slot + a * T * 4 + q * 16, src);
+                constexpr int CPA = T / 4;  // 16-byte pieces per stream array
+                if constexpr (NP > 0 && LPR <= CPA) {
+                    // piece i * LPR + lig: the array is the same for every lane
+#pragma unroll
+                    for (int i = 0; i < (NP + 1) * CPA / LPR; ++i) {
+                        const int a = i * LPR / CPA, q = i * LPR % CPA + lig;
+                        const void *src = a < NP ? (const void *)(p.pidx[a] + base + q * 4)
+                                                 : (const void *)(p.val + base + q * 4);
+                        cp_async16(slot + a * T * 4 + q * 16, src);
+                    }
+                } else {
+                    const int nchunks = nstream * CPA;
+                    for (int c = lig; c < nchunks; c += LPR) {
+                        const int a = c / CPA, q = c % CPA;
+                        const void *src = a < nprod ? (const void *)(p.pidx[a] + base + q * 4)
+                                                    : (const void *)(p.val + base + q * 4);
+                        cp_async16(slot + a * T * 4 + q * 16, src);
+                    }
                 }
                 if (lig == 0) cp_async4(slot + nstream * T * 4, p.bf + (base >> 5));
             }
@@ -261,18 +398,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
         float lsum = 0.f;
 
         // rows between the previous segment's row and this one hold no nonzeros
-        auto fill_gap = [&](int64_t from, int64_t to) {  // rows from+1 .. to-1
-            for (int64_t rr = from + 1; rr < to; ++rr) {
-#pragma unroll
-                for (int c = 0; c < NCH; ++c)
-                    if (act[c]) {
-                        float z[E];
-#pragma unroll
-                        for (int e = 0; e < E; ++e) z[e] = 0.f;
-                        store_row<E>(p.out + rr * R + col[c], z);
-                    }
-            }
-        };
+        auto fill_gap = [&](int64_t from, int64_t to) { zero_rows<E, NCH, LPR>(p.out, R, lig, from, to); };
+        // output row of the current segment
+        float *orow = has_out ? p.out + row * R : nullptr;
         if (has_out && p.segrow && head0) fill_gap(seg > 0 ? (int64_t)__ldg(p.segrow + seg - 1) : -1, row);
 
         // accumulators: the stage sum in registers; once a segment reaches the
@@ -308,52 +436,79 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
         };
         load_target();
 
-        auto fold = [&]() {  // Kahan: segment sum += acc_st
+        auto sidx = [&](int c, int e) -> int { return acc_slot<E, LPR>(c, e, lig); };
+        // Kahan: segment sum += acc_st (the stage sum), acc_st = 0
+        auto fold = [&]() {
 #pragma unroll
-            for (int c = 0; c < NCH; ++c)
+            for (int c = 0; c < NCH; ++c) {
+                if constexpr (E % 4 == 0) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    if (in_smem) {
-                        const float a = s_acc[col[c] + e];
-                        const float y = acc_st[c][e] - s_cmp[col[c] + e];
-                        const float t = a + y;
-                        s_cmp[col[c] + e] = (t - a) - y;
-                        s_acc[col[c] + e] = t;
-                    } else {
-                        s_acc[col[c] + e] = acc_st[c][e];
-                        s_cmp[col[c] + e] = 0.f;
+                    for (int h = 0; h < E / 4; ++h) {
+                        float4 *pa = reinterpret_cast<float4 *>(s_acc + sidx(c, 4 * h));
+                        float4 *pc = reinterpret_cast<float4 *>(s_cmp + sidx(c, 4 * h));
+                        const float *st = &acc_st[c][4 * h];
+                        if (in_smem) {
+                            const float4 A = *pa, C = *pc;
+                            const float a[4] = {A.x, A.y, A.z, A.w}, cm[4] = {C.x, C.y, C.z, C.w};
+                            float t[4], nc[4];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const float y = st[i] - cm[i];
+                                t[i] = a[i] + y;
+                                nc[i] = (t[i] - a[i]) - y;
+                            }
+                            *pa = make_float4(t[0], t[1], t[2], t[3]);
+                            *pc = make_float4(nc[0], nc[1], nc[2], nc[3]);
+                        } else {
+                            *pa = make_float4(st[0], st[1], st[2], st[3]);
+                            *pc = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
                     }
-                    acc_st[c][e] = 0.f;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int i = sidx(c, e);
+                        if (in_smem) {
+                            const float a = s_acc[i];
+                            const float y = acc_st[c][e] - s_cmp[i];
+                            const float t = a + y;
+                            s_cmp[i] = (t - a) - y;
+                            s_acc[i] = t;
+                        } else {
+                            s_acc[i] = acc_st[c][e];
+                            s_cmp[i] = 0.f;
+                        }
+                    }
                 }
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc_st[c][e] = 0.f;
+            }
             in_smem = true;
-        };
-        // the finished segment's value, element e of chunk c
-        auto seg_value = [&](int c, int e) -> double {
-            return in_smem ? (double)s_acc[col[c] + e] - (double)s_cmp[col[c] + e] : (double)acc_st[c][e];
         };
         // hand a finished (or run-cut) segment to its writer
         auto emit = [&](bool starts_before, bool continues_after) {
             if (!has_out) return;
-            if (in_smem) fold();
-            if (!starts_before && !continues_after) {
+            const bool cut = starts_before || continues_after;
+            if (!cut && !in_smem) {  // the common case: the stage sum is the segment
 #pragma unroll
                 for (int c = 0; c < NCH; ++c)
-                    if (act[c]) {
-                        float v[E];
+                    if (act[c]) store_row<E>(orow + col[c], acc_st[c]);
+                return;
+            }
+            SegAcc<E, NCH> a;
 #pragma unroll
-                        for (int e = 0; e < E; ++e) v[e] = (float)seg_value(c, e);
-                        store_row<E>(p.out + row * R + col[c], v);
-                    }
-            } else {
-                const int slot = 2 * g + (first ? 0 : 1);
+            for (int c = 0; c < NCH; ++c)
 #pragma unroll
-                for (int c = 0; c < NCH; ++c)
-#pragma unroll
-                    for (int e = 0; e < E; ++e) s_part[(size_t)slot * RT + col[c] + e] = seg_value(c, e);
-                if (lig == 0) {
-                    s_pseg[slot] = seg;
-                    s_pflag[slot] = (starts_before ? 1 : 0) | (continues_after ? 2 : 0);
-                }
+                for (int e = 0; e < E; ++e) a.v[c][e] = acc_st[c][e];
+            const int slot = 2 * g + (first ? 0 : 1);
+            double *part = cut ? part_ptr(slot) : nullptr;
+            if constexpr (NP == 1)  // short segments: emitted often, one out-of-line copy
+                emit_segment_outlined<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, R, orow, part);
+            else  // calls would cost the register-heavy variants spills in the hot loop
+                emit_segment_body<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, R, orow, part);
+            if (cut && lig == 0) {
+                s_pseg[slot] = seg;
+                s_pflag[slot] = (starts_before ? 1 : 0) | (continues_after ? 2 : 0);
             }
         };
         // a new segment starts at this nonzero
@@ -365,10 +520,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
             for (int c = 0; c < NCH; ++c)
 #pragma unroll
                 for (int e = 0; e < E; ++e) acc_st[c][e] = 0.f;
-            const int64_t prev = row;
             ++seg;
-            row = p.segrow ? (int64_t)__ldg(p.segrow + seg) : seg;
-            if (has_out && p.segrow) fill_gap(prev, row);
+            if (p.segrow) {
+                const int64_t prev = row;
+                row = (int64_t)__ldg(p.segrow + seg);
+                if (has_out) {
+                    fill_gap(prev, row);
+                    orow = p.out + row * R;
+                }
+            } else {
+                ++row;
+                if (has_out) orow += R;
+            }
             load_target();
         };
         // acc_st += w * (brow * row), w = val (KIND 0) or the residual weight
@@ -453,11 +616,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
 
         // ---- software pipeline over quarters of a stage (Q nonzeros; 4, or 2
         // when a lane holds more than 4 columns): the gathers of quarter h+1
-        // are in flight while quarter h is consumed.  Full stages are unrolled
-        // (static offsets and masks); the first quarter of the next stage is
-        // requested while the last quarter of the current one is consumed.
+        // are in flight while quarter h is consumed.  A full stage is walked
+        // by a rolled loop over pairs of quarters (two register buffers); the
+        // first quarter of the next stage is requested while the last quarter
+        // of the current one is consumed.
         constexpr int Q = E * NCH <= 4 ? 4 : 2;
-        constexpr int QPS = T / Q;  // quarters per stage
+        constexpr int QPS = T / Q;  // quarters per stage (even)
+        static_assert(QPS % 2 == 0, "quarters are consumed in pairs");
         // the unrolled pipeline serves the 3-way SpMTTKRP and SpTTM vector
         // variants; the general-N and scalar ones walk nonzeros one at a time
         constexpr bool PIPE = (NP == 1 || NP == 2) && E > 1;
@@ -515,8 +680,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                     const bool f = (fcm >> q) & 1u;
 #pragma unroll
                     for (int c = 0; c < NCH; ++c)
-                        b.br[q][c] = f ? IO::load(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)jj[q] * Rb))
-                                       : IO::zero();
+                        b.br[q][c] = IO::load_if(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)jj[q] * Rb), f);
                 }
             }
             b.fcm = fcm;
@@ -608,28 +772,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
             if (PIPE && cnt == T) {
                 if (!have_first) prefetch(qa, slot, 0, hw);
                 have_first = false;
-#pragma unroll
-                for (int qt = 0; qt < QPS; ++qt) {
-                    Quarter &cur = (qt & 1) ? qb : qa;
-                    Quarter &nxt = (qt & 1) ? qa : qb;
-                    if (qt + 1 < QPS) {
-                        prefetch(nxt, slot, qt + 1, hw);
+                // quarters in pairs (qa, qb alternate), the loop kept rolled so
+                // that the code stays small
+#pragma unroll 1
+                for (int qt = 0; qt < QPS; qt += 2) {
+                    prefetch(qb, slot, qt + 1, hw);
+                    consume(qa, slot, qt, (hw >> (qt * Q)) & ((1u << Q) - 1u), base);
+                    if (qt + 2 < QPS) {
+                        prefetch(qa, slot, qt + 2, hw);
                     } else if (s + 1 < nst && r1 - (base + T) >= T) {
                         // the next stage is full: request its first quarter now
                         cp_async_wait<NS - 2>();
                         __syncwarp(gmask);
                         const unsigned char *nslot = ring + ((s + 1) % NS) * sbytes;
-                        prefetch(nxt, nslot, 0, *reinterpret_cast<const uint32_t *>(nslot + nstream * T * 4));
+                        prefetch(qa, nslot, 0, *reinterpret_cast<const uint32_t *>(nslot + nstream * T * 4));
                         have_first = true;
                     }
-                    consume(cur, slot, qt, (hw >> (qt * Q)) & ((1u << Q) - 1u), base);
+                    consume(qb, slot, qt + 1, (hw >> ((qt + 1) * Q)) & ((1u << Q) - 1u), base);
                 }
             } else {
                 process_tail(slot, base, hw, cnt);
             }
             fold();  // stage sums folded every 32 nonzeros
         }
-        // ---- end of run: the last segment
+        // ---- end of run: the last segment (its partial may go to the ring
+        // region, so every lane of the group must be done with the ring)
+        cp_async_wait<0>();
+        __syncwarp(gmask);
         const bool ends_here = (r1 == p.nnz) || head_at(p, r1);
         emit(first && !head0, !ends_here);
         if (has_out && p.segrow && r1 == p.nnz) fill_gap(row, p.out_rows);
@@ -674,7 +843,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                 cur_first_e = e;
             }
             cur_last_e = e;
-            sum += s_part[(size_t)e * RT + t];
+            sum += part_ptr(e)[t];
         }
         flush();
     }
@@ -758,8 +927,7 @@ int launch_variant(StreamParams &p, cudaStream_t s) {
     constexpr int G = kThreads / LPR;
     constexpr int RT = NCH * LPR * E;
     auto kern = k_stream<TF, E, LPR, NCH, NP, KIND>;
-    const size_t smem = (size_t)G * group_stride(p.nprod + 1) + (size_t)2 * G * RT * 8 + (size_t)2 * G * 8 +
-                        (size_t)2 * G * 4 + (size_t)G * 4 + (size_t)G * 2 * RT * 4;
+    const size_t smem = stream_smem_bytes(p.nprod + 1, G, RT);
     static size_t cached_smem = 0;
     static int cached_occ = 0;
     if (cached_smem != smem) {
@@ -798,15 +966,15 @@ int launch_np(StreamParams &p, cudaStream_t s) {
     }
 }
 
-// 16-byte lanes: E = 16 / sizeof(TF) elements each
-template <typename TF, int E, int KIND>
-int launch_vec(StreamParams &p, cudaStream_t s) {
-    const int chunks = p.R / E;
-    if (chunks <= 4) return launch_np<TF, E, 4, 1, KIND>(p, s);
-    if (chunks <= 8) return launch_np<TF, E, 8, 1, KIND>(p, s);
-    if (chunks <= 16) return launch_np<TF, E, 16, 1, KIND>(p, s);
-    if (chunks <= 32) return launch_np<TF, E, 32, 1, KIND>(p, s);
-    if constexpr (E == 4) return launch_np<TF, E, 32, 2, KIND>(p, s);
+// eight columns per lane (FP32: one 32-byte load per row, BF16: one 16-byte
+// load), lane groups of 4..32 lanes for R up to 256
+template <typename TF, int KIND>
+int launch_v8(StreamParams &p, cudaStream_t s) {
+    const int chunks = (p.R + 7) / 8;
+    if (chunks <= 4) return launch_np<TF, 8, 4, 1, KIND>(p, s);
+    if (chunks <= 8) return launch_np<TF, 8, 8, 1, KIND>(p, s);
+    if (chunks <= 16) return launch_np<TF, 8, 16, 1, KIND>(p, s);
+    if (chunks <= 32) return launch_np<TF, 8, 32, 1, KIND>(p, s);
     return fail(FCOO_ERR_UNSUPPORTED, "R=%d above the supported rank", p.R);
 }
 
@@ -820,15 +988,26 @@ int launch_scalar(StreamParams &p, cudaStream_t s) {
     return launch_variant<TF, 1, 32, 8, 0, KIND>(p, s);
 }
 
-bool aligned16(const void *q) { return q == nullptr || ((uintptr_t)q & 15u) == 0; }
+bool aligned(const void *q, uintptr_t a) { return q == nullptr || ((uintptr_t)q & (a - 1)) == 0; }
 
-// 16-byte lanes when R is a multiple of the vector width and every row
-// pointer is 16-byte aligned, scalar lanes otherwise.
-template <typename TF, int E, int KIND>
+// Lane layout by factor type, rank and alignment: eight columns per lane
+// when R is a multiple of 8 (FP32 from R = 24 on; rows 32-byte aligned),
+// four FP32 columns per lane in groups of 4 for R <= 16, scalar lanes
+// otherwise.
+template <typename TF, int KIND>
 int launch_typed(StreamParams &p, cudaStream_t s) {
-    bool vec = p.R % E == 0 && aligned16(p.out) && aligned16(p.T);
-    for (int m = 0; m < p.nprod; ++m) vec = vec && aligned16(p.F[m]);
-    return vec ? launch_vec<TF, E, KIND>(p, s) : launch_scalar<TF, KIND>(p, s);
+    auto all_aligned = [&](uintptr_t a) {
+        bool ok = aligned(p.out, 16) && aligned(p.T, a);
+        for (int m = 0; m < p.nprod; ++m) ok = ok && aligned(p.F[m], a);
+        return ok;
+    };
+    if constexpr (std::is_same<TF, float>::value) {
+        if (p.R % 4 == 0 && p.R <= 16 && all_aligned(16)) return launch_np<TF, 4, 4, 1, KIND>(p, s);
+        if (p.R % 8 == 0 && all_aligned(32)) return launch_v8<TF, KIND>(p, s);
+    } else {
+        if (p.R % 8 == 0 && all_aligned(16)) return launch_v8<TF, KIND>(p, s);
+    }
+    return launch_scalar<TF, KIND>(p, s);
 }
 
 }  // namespace
