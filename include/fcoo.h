@@ -294,6 +294,14 @@ int cp_als_iter(const fcoo_t *const *Xn, cp_state_t *st, fcoo_stream_t stream);
  * the number of completed sweeps and the number of pseudo-inverse solves. */
 int cp_state_stats(const cp_state_t *st, double *lambda, double *fit, int *iters, int *npinv, fcoo_stream_t stream);
 
+/* Change the storage type of the factors (FCOO_F32 <-> FCOO_BF16) in place:
+ * BF16 -> FP32 is exact; FP32 -> BF16 rounds to nearest even and recomputes
+ * the Grams.  Later cp_als_iter sweeps gather the factors in the new type.
+ * This serves a mixed-precision schedule (BF16 sweeps while the fit moves,
+ * FP32 sweeps to finish); the paper's Algorithm 1 has one precision
+ * throughout.  Asynchronous on `stream`. */
+int cp_state_set_dtype(cp_state_t *st, int dtype, fcoo_stream_t stream);
+
 /* Copy factor k as float32 (dims[k] x R) to host or device memory. Synchronous. */
 int cp_state_copy_factor(const cp_state_t *st, int k, float *dst, fcoo_stream_t stream);
 

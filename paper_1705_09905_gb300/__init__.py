@@ -243,6 +243,14 @@ class CPState:
             check(lib.cp_als_iter(ctypes.cast(hs, ctypes.POINTER(ctypes.c_void_p)), self._h, _stream(stream)))
         return self
 
+    def set_dtype(self, dtype, stream=None):
+        """Change the factor storage type in place (``cp_state_set_dtype``):
+        BF16 -> FP32 is exact, FP32 -> BF16 rounds and recomputes the Grams."""
+        code = BF16 if dtype == torch.bfloat16 else F32
+        check(lib.cp_state_set_dtype(self._h, code, _stream(stream)))
+        self.dtype = dtype
+        return self
+
     def stats(self, stream=None):
         lam = np.empty(self.R, np.float64)
         fit = ctypes.c_double()

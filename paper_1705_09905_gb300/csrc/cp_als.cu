@@ -535,7 +535,9 @@ extern "C" int cp_state_create(int nmodes, const uint32_t *dims, int R, int dtyp
         st->dims[k] = dims[k];
         st->max_dim = std::max<int64_t>(st->max_dim, dims[k]);
     }
-    const size_t es = dtype == FCOO_BF16 ? 2 : 4;
+    // factor buffers are FP32-sized for either dtype, so that
+    // cp_state_set_dtype can change the storage in place
+    const size_t es = 4;
     const int64_t nbmax = max_blocks(st->max_dim);
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -600,6 +602,35 @@ extern "C" int cp_state_create(int nmodes, const uint32_t *dims, int R, int dtyp
         return rc;
     }
     *out = st;
+    return FCOO_OK;
+}
+
+extern "C" int cp_state_set_dtype(cp_state_t *st, int dtype, fcoo_stream_t stream) {
+    clear_error();
+    if (!st) return fail(FCOO_ERR_INVALID_ARG, "cp_state_set_dtype: NULL state");
+    if (dtype != FCOO_F32 && dtype != FCOO_BF16) return fail(FCOO_ERR_INVALID_ARG, "cp_state_set_dtype: bad dtype");
+    if (dtype == st->dtype) return FCOO_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < st->nmodes; ++k) {
+        const int64_t n = (int64_t)st->dims[k] * st->R;
+        if (dtype == FCOO_F32) {
+            // BF16 -> FP32 is exact: the Grams of the stored factors stay valid
+            k_to_f32<<<gs(n), 256, 0, s>>>((const __nv_bfloat16 *)st->F[k], n, st->Fu);
+            FCOO_CUDA(cudaGetLastError());
+            FCOO_CUDA(cudaMemcpyAsync(st->F[k], st->Fu, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+        } else {
+            // FP32 -> BF16 rounds: the Grams are recomputed from the rounded factors
+            FCOO_CUDA(cudaMemcpyAsync(st->Fu, st->F[k], (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+            k_to_dtype<<<gs(n), 256, 0, s>>>(st->Fu, n, (__nv_bfloat16 *)st->F[k]);
+            FCOO_CUDA(cudaGetLastError());
+        }
+    }
+    st->dtype = dtype;
+    if (dtype == FCOO_BF16)
+        for (int k = 0; k < st->nmodes; ++k) {
+            const int rc = gram_of(st, k, s);
+            if (rc) return rc;
+        }
     return FCOO_OK;
 }
 

@@ -71,6 +71,45 @@ def test_bf16_sweep_matches_oracle_with_same_rounding(fc, oracle):
             assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 2e-3, (sweep, k)
 
 
+def test_mixed_schedule_switches_storage(fc, oracle):
+    """BF16 sweeps, then cp_state_set_dtype(FP32) and FP32 sweeps: the switch
+    keeps the factors exactly (BF16 -> FP32 is exact) and the FP32 sweeps
+    that follow match the oracle continued from the same factors."""
+    cfg = synth.CONFIGS["tiny"]
+    T = synth.make_tensor(cfg)
+    Xs = handles(fc, T)
+    R = 8
+    init = synth.make_factors(T.dims, R, seed=5, kind="uniform")
+    st = fc.CPState(T.dims, R, init, dtype=torch.bfloat16)
+    st.iterate(Xs, sweeps=2)
+    before = [st.factor(k).cpu().numpy() for k in range(3)]
+    lam0 = st.stats()["lambda"]
+    st.set_dtype(torch.float32)
+    after = [st.factor(k).cpu().numpy() for k in range(3)]
+    for k in range(3):
+        assert np.array_equal(before[k], after[k])
+        t = torch.from_numpy(after[k])
+        assert torch.equal(t.to(torch.bfloat16).float(), t)  # still the BF16 values
+    idx, val = T.idx_u32(), T.val.double().numpy()
+    F = [b.astype(np.float64) for b in before]
+    lam = lam0
+    for sweep in range(2):
+        st.iterate(Xs)
+        for n in range(3):
+            F, lam, _, _ = oracle.cp_als_mode(T.dims, idx, val, F, n)
+        s = st.stats()
+        assert abs(s["fit"] - oracle.cp_fit(T.dims, idx, val, F, lam)) <= 1e-5
+        for k in range(3):
+            assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 1e-4, (sweep, k)
+    # and back: FP32 -> BF16 rounds to nearest even
+    f32 = [st.factor(k).cpu() for k in range(3)]
+    st.set_dtype(torch.bfloat16)
+    for k in range(3):
+        assert torch.equal(st.factor(k).cpu(), f32[k].to(torch.bfloat16).float())
+    st.iterate(Xs)
+    assert np.isfinite(st.stats()["fit"])
+
+
 def test_pseudo_inverse_fallback(fc, oracle):
     # modes 1 and 2 of size 1: the mode-0 normal matrix G1 * G2 has rank 1 < R
     T = synth.random_small((50, 1, 1), 30, seed=5)
