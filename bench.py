@@ -518,7 +518,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--nnz", type=int, default=0, help="scale the workload to this many nonzeros (same dims)")
     ap.add_argument("--rank", type=int, default=0, help="override R")
-    ap.add_argument("--cpu-sample", type=int, default=8_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=40_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--part", default="all", choices=["all", "spttm"],
                     help="spttm: only the SpTTM line (4-way workload, --nnz scales it), for profiling")

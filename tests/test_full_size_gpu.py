@@ -1,0 +1,167 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times (default grid, threadlen 8):
+
+* SpMTTKRP on the skewed 3-way tensor (76M nonzeros, R = 32, FP32), every
+  output element of all three modes against the FP64 oracle;
+* one CP-ALS sweep (Algorithm 1, R = 64, FP32 storage) on the same tensor,
+  each mode update against the oracle's update from the same factors;
+* SpTTM on the 4-way tensor (100M nonzeros, 51M fibres, R = 16): sampled
+  fibres against the oracle on their nonzeros, and the column sums of the
+  whole result against the closed form sum_p val_p U(k_p, :);
+* the sparse CP-fit loss and gradients on the 20M-nonzero observed set
+  against the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import assert_close_abs, host_factors, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import paper_1705_09905_gb300 as fc
+
+    return fc
+
+
+def host_coo(T):
+    return [a.cpu().numpy().astype(np.uint32) for a in T.idx], T.val.double().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def skewed3(fc):
+    cfg = synth.CONFIGS["skewed3"]
+    dev = torch.device("cuda", 0)
+    T = synth.make_tensor(cfg, device=dev)
+    idx32 = [a.to(torch.int32).contiguous() for a in T.idx]
+    Xs = [fc.FCOO.build(idx32, T.val, cfg.dims, n, "mttkrp", 8) for n in range(3)]
+    idx, val = host_coo(T)
+    del T, idx32
+    yield cfg, Xs, idx, val
+    for X in Xs:
+        X.close()
+    torch.cuda.empty_cache()
+
+
+def test_spmttkrp_full_size_every_element(fc, oracle, skewed3):
+    cfg, Xs, idx, val = skewed3
+    F = [f.to("cuda") for f in synth.make_factors(cfg.dims, cfg.R, seed=1)]
+    Fh = host_factors(F)
+    absF = [np.abs(f) for f in Fh]
+    for n in range(3):
+        got = fc.spmttkrp(Xs[n], F).cpu().numpy()
+        ref = oracle.mttkrp(cfg.dims, idx, val, Fh, n)
+        absref = oracle.mttkrp(cfg.dims, idx, np.abs(val), absF, n)
+        assert_close_abs(got, ref, absref)
+
+
+def test_cp_als_full_size_one_sweep(fc, oracle, skewed3):
+    """One sweep at R = 64, each mode update checked on its own: the oracle
+    takes the factors the device held when it made that update (the start
+    factors, then the device's updated ones), so errors do not compound.
+
+    On this Zipf tensor the first two updates pull every column towards the
+    hot slices, and the last update's normal matrix V has cond(V) ~ 1e6..1e7
+    (computed below).  FP32 rounding of M (~1e-7) then moves that factor by
+    up to cond(V) * 1e-7 along directions the data barely determine, in any
+    FP32 path, so the forward error of a factor is bounded only where V is
+    well conditioned.  For every update the least-squares objective is
+    bounded instead: the fit of the device's model (evaluated by the oracle
+    in FP64) is within 1e-4 of the fit of the oracle's own FP64 update from
+    the same factors, and the device's fit value agrees with the oracle's
+    evaluation of the device's model."""
+    cfg, Xs, idx, val = skewed3
+    R = 64
+    for kind in ("normal", "uniform"):
+        init = synth.make_factors(cfg.dims, R, seed=0, kind=kind)
+        st = fc.CPState(cfg.dims, R, init)
+        st.iterate(Xs)
+        s = st.stats()
+        dev = [st.factor(k).cpu().double().numpy() for k in range(3)]
+        st.close()
+        start = [f.double().numpy() for f in init]
+        assert s["npinv"] == 0
+        for n in range(3):
+            given = [dev[k] if k < n else start[k] for k in range(3)]
+            V = np.ones((R, R))
+            for k in range(3):
+                if k != n:
+                    V *= given[k].T @ given[k]
+            F, lam, _, used = oracle.cp_als_mode(cfg.dims, idx, val, given, n)
+            assert not used
+            if np.linalg.cond(V) < 1e3:
+                assert rel_fro(dev[n], F[n]) <= 1e-4, (kind, n, rel_fro(dev[n], F[n]))
+        # the last update: objective, and the device's own fit evaluation
+        fit_dev_model = oracle.cp_fit(cfg.dims, idx, val, dev, s["lambda"])
+        fit_orc_update = oracle.cp_fit(cfg.dims, idx, val, F, lam)
+        assert abs(s["fit"] - fit_dev_model) <= 1e-5, (kind, s["fit"], fit_dev_model)
+        assert -1e-6 <= fit_orc_update - fit_dev_model <= 1e-4, (kind, fit_orc_update, fit_dev_model)
+
+
+def test_spttm_full_size_sampled_fibres_and_column_sums(fc, oracle):
+    cfg = synth.CONFIGS["ttm4"]
+    dev = torch.device("cuda", 0)
+    T = synth.make_tensor(cfg, device=dev)
+    idx32 = [a.to(torch.int32).contiguous() for a in T.idx]
+    X = fc.FCOO.build(idx32, T.val, cfg.dims, 3, "ttm", 8)
+    U = synth.make_factors([cfg.dims[3]], 16, seed=1, device=dev)[0]
+    Y = fc.spttm(X, U)
+    torch.cuda.synchronize()
+    keys = X.fibre_indices()  # nfib x 3 index tuples, in the order of Y's rows
+    assert keys.shape == (X.nseg, 3)
+    Uh = U.double().cpu().numpy()
+    val = T.val.double().cpu().numpy()
+    k = T.idx[3].cpu().numpy()
+    # closed form over the whole result: sum over fibres of Y = sum_p val_p U(k_p, :)
+    colsum = Y.double().sum(0).cpu().numpy()
+    ref_colsum = np.bincount(k, weights=val, minlength=cfg.dims[3]) @ Uh
+    absref_colsum = np.bincount(k, weights=np.abs(val), minlength=cfg.dims[3]) @ np.abs(Uh)
+    assert np.all(np.abs(colsum - ref_colsum) <= 1e-6 * absref_colsum)
+    # sampled fibres (and the first and last) against the oracle on their nonzeros
+    rng = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([[0, X.nseg - 1], rng.choice(X.nseg, 254, replace=False)]))
+    dims = cfg.dims
+    lin = lambda a, b, c: (a.astype(np.int64) * dims[1] + b) * dims[2] + c
+    want = torch.as_tensor(lin(keys[rows, 0], keys[rows, 1], keys[rows, 2]), device=dev)
+    fkey = (T.idx[0] * dims[1] + T.idx[1]) * dims[2] + T.idx[2]
+    sel = torch.isin(fkey, want).nonzero().squeeze(1).cpu().numpy()
+    sub_idx = [a.cpu().numpy()[sel].astype(np.uint32) for a in T.idx]
+    okeys, oy = oracle.ttm(dims, sub_idx, val[sel], Uh, 3)
+    _, oabs = oracle.ttm(dims, sub_idx, np.abs(val[sel]), np.abs(Uh), 3)
+    assert okeys.shape[0] == rows.size
+    order = np.lexsort((okeys[:, 2], okeys[:, 1], okeys[:, 0]))
+    got_rows = Y[torch.as_tensor(rows, device=dev)].cpu().numpy()
+    gk = keys[rows]
+    gorder = np.lexsort((gk[:, 2], gk[:, 1], gk[:, 0]))
+    assert np.array_equal(okeys[order].astype(np.int64), gk[gorder].astype(np.int64))
+    assert_close_abs(got_rows[gorder], oy[order], oabs[order])
+    del Y, X, T, idx32, fkey
+    torch.cuda.empty_cache()
+
+
+def test_sparse_fit_full_size(fc, oracle):
+    cfg = synth.CONFIGS["fit3"]
+    dev = torch.device("cuda", 0)
+    T = synth.make_tensor(cfg, device=dev)
+    idx32 = [a.to(torch.int32).contiguous() for a in T.idx]
+    Xs = [fc.FCOO.build(idx32, T.val, cfg.dims, n, "mttkrp", 8) for n in range(3)]
+    R = cfg.R
+    F = [(f * R ** (-1.0 / 6.0)).to(dev) for f in synth.make_factors(cfg.dims, R, seed=2)]
+    loss, grads, dv = fc.sparse_fit_grad(Xs, F, want_dvals=True)
+    torch.cuda.synchronize()
+    idx, val = host_coo(T)
+    Fh = host_factors(F)
+    rl, rg, rdv = oracle.sparse_fit(cfg.dims, idx, val, Fh)
+    assert abs(loss.item() - rl) <= 1e-5 * rl
+    e = np.abs(rdv)
+    np.testing.assert_allclose(dv.cpu().numpy(), rdv, rtol=1e-4, atol=1e-5 * e.max())
+    for n in range(3):
+        absn = oracle.mttkrp(cfg.dims, idx, e, [np.abs(f) for f in Fh], n)
+        assert_close_abs(grads[n].cpu().numpy(), rg[n], absn + 1e-30)
+    for X in Xs:
+        X.close()
+    torch.cuda.empty_cache()

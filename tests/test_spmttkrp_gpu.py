@@ -94,7 +94,7 @@ def test_single_nonzero_and_ragged_sizes(fc, oracle):
         run_mttkrp(fc, oracle, T, 16, nnz % 3)
 
 
-@pytest.mark.parametrize("tl", [8, 16, 32, 64])
+@pytest.mark.parametrize("tl", [1, 2, 4, 8, 16, 32, 64])
 def test_threadlen_values(fc, oracle, tl):
     T = synth.random_small((100, 90, 80), 50_000, seed=tl)
     run_mttkrp(fc, oracle, T, 32, 0, tl=tl)
@@ -126,6 +126,23 @@ def run_ttm(fc, oracle, T, R, mode, dtype=torch.float32, tl=8):
     _, absref = oracle.ttm(dims, idx, np.abs(val), np.abs(Uh), mode)
     np.testing.assert_array_equal(X.fibre_indices(), keys)
     assert_close_abs(got.cpu().numpy(), ref, absref)
+
+
+@pytest.mark.parametrize("R,dtype", [(32, torch.float32), (16, torch.float32), (32, torch.bfloat16)])
+def test_unaligned_factor_rows_take_the_scalar_path(fc, oracle, R, dtype):
+    # factor storage starting 4 (2) bytes past an aligned address: the vector
+    # lane layouts need 16/32-byte aligned rows, so the scalar lanes run
+    T = synth.make_tensor(synth.scaled(synth.CONFIGS["skewed3"], 200_000, dims=(300, 200, 400)))
+    base = synth.make_factors(T.dims, R, seed=6)
+    factors = []
+    for f in base:
+        buf = torch.empty(f.numel() + 1, dtype=dtype, device="cuda")
+        v = buf[1:].view(f.shape)
+        v.copy_(f.to(dtype))
+        assert v.data_ptr() % 16 != 0
+        factors.append(v)
+    for mode in range(3):
+        run_mttkrp(fc, oracle, T, R, mode, dtype=dtype, factors=factors)
 
 
 def test_ttm_tiny_config(fc, oracle):
