@@ -520,13 +520,24 @@ def main():
     ap.add_argument("--rank", type=int, default=0, help="override R")
     ap.add_argument("--cpu-sample", type=int, default=40_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
-    ap.add_argument("--part", default="all", choices=["all", "spttm"],
-                    help="spttm: only the SpTTM line (4-way workload, --nnz scales it), for profiling")
+    ap.add_argument("--part", default="all", choices=["all", "spttm", "cp", "fit"],
+                    help="only one extra line, for profiling: spttm (4-way workload, --nnz scales it), "
+                         "cp (CP-ALS on the skewed 3-way workload) or fit (sparse CP fit)")
+    ap.add_argument("--sweeps", type=int, default=20, help="CP-ALS sweeps of the cp line")
     args = ap.parse_args()
-    if args.part == "spttm":
+    if args.part != "all":
         import paper_1705_09905_gb300 as fc
 
-        print(json.dumps(bench_spttm(fc, torch.device("cuda", 0), args.quick, args.nnz)), flush=True)
+        dev = torch.device("cuda", 0)
+        if args.part == "spttm":
+            line = bench_spttm(fc, dev, args.quick, args.nnz)
+        elif args.part == "fit":
+            line = bench_sparse_fit(fc, dev, args.quick)
+        else:
+            cfg = workload_config(args)
+            _, Xs, _, _ = build_workload(cfg, dev)
+            line = bench_cp_als(fc, Xs, cfg.dims, args.sweeps)
+        print(json.dumps(line), flush=True)
         return
     if args.impl == "reference":
         args.steps = 5 if args.steps is None else args.steps

@@ -106,81 +106,13 @@ struct GramList {
     int n;
 };
 
-// One CTA.  V = Hadamard of the listed Grams; W = V^-1 via FP64 Cholesky,
-// or, when a pivot d <= kRankTol * max diag(V), the Moore-Penrose inverse from
-// a cyclic Jacobi eigendecomposition dropping |w| <= kRankTol * max |w|.
-__global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, double *V, double *Q, double *W,
-                                                         float *Wf, int *flags) {
+// Moore-Penrose inverse of the normal matrix held in Q (V is work space) from
+// a cyclic Jacobi eigendecomposition, dropping eigenvalues |w| <= kRankTol *
+// max |w|; W = the inverse (FP64), Wf = its FP32 split.  Whole CTA.
+__device__ void pinv_jacobi(int R, double *V, double *Q, double *W, float *Wf, int *flags) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    __shared__ double s_dmax, s_c, s_s;
-    __shared__ int s_ok, s_done;
-    for (int e = tid; e < R * R; e += nt) {
-        double v = 1.0;
-        for (int k = 0; k < gl.n; ++k) v *= gl.g[k][e];
-        V[e] = v;
-        Q[e] = v;  // copy kept for the eigen fallback
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double m = 0.0;
-        int finite = 1;
-        for (int i = 0; i < R; ++i) m = fmax(m, V[i * R + i]);
-        for (int e = 0; e < R * R; ++e) finite &= isfinite(V[e]) ? 1 : 0;
-        if (!finite) atomicOr(flags + 1, 1);
-        s_dmax = m;
-        s_ok = (m > 0.0 && finite) ? 1 : 0;
-    }
-    __syncthreads();
-    // right-looking Cholesky in place (lower triangle)
-    for (int j = 0; j < R && s_ok; ++j) {
-        if (tid == 0) {
-            double d = V[j * R + j];
-            if (!(d > kRankTol * s_dmax)) s_ok = 0;
-            else V[j * R + j] = sqrt(d);
-        }
-        __syncthreads();
-        if (!s_ok) break;
-        const double ljj = V[j * R + j];
-        for (int i = j + 1 + tid; i < R; i += nt) V[i * R + j] /= ljj;
-        __syncthreads();
-        const int m = R - j - 1;
-        for (int e = tid; e < m * m; e += nt) {
-            int i = j + 1 + e / m, k = j + 1 + e % m;
-            if (k <= i) V[i * R + k] -= V[i * R + j] * V[k * R + j];
-        }
-        __syncthreads();
-    }
-    if (s_ok) {
-        // W = L^-T L^-1: column c of L^-1 by forward substitution (thread c),
-        // kept in the upper triangle of W transposed: W[c*R + i] = Linv[i][c]
-        for (int c = tid; c < R; c += nt) {
-            for (int i = 0; i < R; ++i) {
-                double s = (i == c) ? 1.0 : 0.0;
-                if (i < c) {
-                    W[c * R + i] = 0.0;
-                    continue;
-                }
-                for (int k = c; k < i; ++k) s -= V[i * R + k] * W[c * R + k];
-                W[c * R + i] = s / V[i * R + i];
-            }
-        }
-        __syncthreads();
-        // V <- (L^-1)^T L^-1 ; entry (a,b) = sum_k Linv[k][a] Linv[k][b]
-        for (int e = tid; e < R * R; e += nt) {
-            int a = e / R, b = e % R;
-            int k0 = a > b ? a : b;
-            double s = 0.0;
-            for (int k = k0; k < R; ++k) s += W[a * R + k] * W[b * R + k];
-            V[e] = s;
-        }
-        __syncthreads();
-        for (int e = tid; e < R * R; e += nt) {
-            W[e] = V[e];
-            split_store(Wf, R * R, e, V[e]);
-        }
-        return;
-    }
-    // ---- pseudo-inverse through the symmetric eigendecomposition
+    __shared__ double s_c, s_s;
+    __shared__ int s_done;
     if (tid == 0) atomicAdd(flags, 1);
     // A (in V) <- copy of the normal matrix, Q (eigenvectors) <- I
     for (int e = tid; e < R * R; e += nt) {
@@ -255,6 +187,202 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, dou
     }
     __syncthreads();
     for (int e = tid; e < R * R; e += nt) split_store(Wf, R * R, e, W[e]);
+}
+
+// One CTA.  V = Hadamard of the listed Grams; W = V^-1 via FP64 Cholesky,
+// or, when a pivot d <= kRankTol * max diag(V), the Moore-Penrose inverse from
+// a cyclic Jacobi eigendecomposition dropping |w| <= kRankTol * max |w|.
+__global__ void __launch_bounds__(kSolveThreads) k_solve(GramList gl, int R, double *V, double *Q, double *W,
+                                                         float *Wf, int *flags) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double s_dmax;
+    __shared__ int s_ok;
+    for (int e = tid; e < R * R; e += nt) {
+        double v = 1.0;
+        for (int k = 0; k < gl.n; ++k) v *= gl.g[k][e];
+        V[e] = v;
+        Q[e] = v;  // copy kept for the eigen fallback
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        int finite = 1;
+        for (int i = 0; i < R; ++i) m = fmax(m, V[i * R + i]);
+        for (int e = 0; e < R * R; ++e) finite &= isfinite(V[e]) ? 1 : 0;
+        if (!finite) atomicOr(flags + 1, 1);
+        s_dmax = m;
+        s_ok = (m > 0.0 && finite) ? 1 : 0;
+    }
+    __syncthreads();
+    // right-looking Cholesky in place (lower triangle)
+    for (int j = 0; j < R && s_ok; ++j) {
+        if (tid == 0) {
+            double d = V[j * R + j];
+            if (!(d > kRankTol * s_dmax)) s_ok = 0;
+            else V[j * R + j] = sqrt(d);
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const double ljj = V[j * R + j];
+        for (int i = j + 1 + tid; i < R; i += nt) V[i * R + j] /= ljj;
+        __syncthreads();
+        const int m = R - j - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) V[i * R + k] -= V[i * R + j] * V[k * R + j];
+        }
+        __syncthreads();
+    }
+    if (s_ok) {
+        // W = L^-T L^-1: column c of L^-1 by forward substitution (thread c),
+        // kept in the upper triangle of W transposed: W[c*R + i] = Linv[i][c]
+        for (int c = tid; c < R; c += nt) {
+            for (int i = 0; i < R; ++i) {
+                double s = (i == c) ? 1.0 : 0.0;
+                if (i < c) {
+                    W[c * R + i] = 0.0;
+                    continue;
+                }
+                for (int k = c; k < i; ++k) s -= V[i * R + k] * W[c * R + k];
+                W[c * R + i] = s / V[i * R + i];
+            }
+        }
+        __syncthreads();
+        // V <- (L^-1)^T L^-1 ; entry (a,b) = sum_k Linv[k][a] Linv[k][b]
+        for (int e = tid; e < R * R; e += nt) {
+            int a = e / R, b = e % R;
+            int k0 = a > b ? a : b;
+            double s = 0.0;
+            for (int k = k0; k < R; ++k) s += W[a * R + k] * W[b * R + k];
+            V[e] = s;
+        }
+        __syncthreads();
+        for (int e = tid; e < R * R; e += nt) {
+            W[e] = V[e];
+            split_store(Wf, R * R, e, V[e]);
+        }
+        return;
+    }
+    pinv_jacobi(R, V, Q, W, Wf, flags);
+}
+
+// Largest R whose normal matrix and triangular inverse both fit in shared memory.
+constexpr int kSolveSmemMaxR = 112;
+
+// The same solve with the matrices in shared memory (R <= kSolveSmemMaxR),
+// for the FP64 rate of GB300 and to keep each step off the memory system:
+//  * V = Hadamard of the Grams; max diag(V) and finiteness by block reduction;
+//  * right-looking Cholesky with one barrier per column: step j updates the
+//    trailing triangle with the unscaled column, A(i,k) -= A(i,j) A(k,j) / d_j
+//    (= l_ij l_kj), and scales column j-1 to L in the same phase;
+//  * Y = L^-1 column by column (one thread per column, no barrier);
+//  * W = Y^T Y on the upper triangle, mirrored, and split to FP32 hi + lo.
+// A non-positive pivot d_j <= kRankTol * max diag(V) (or a non-finite V) sends
+// the whole CTA to the Jacobi pseudo-inverse, as in k_solve.
+__global__ void __launch_bounds__(kSolveThreads) k_solve_smem(GramList gl, int R, double *V, double *Q, double *W,
+                                                              float *Wf, int *flags) {
+    extern __shared__ double sd[];
+    double *A = sd;          // R x R: V, then L in the lower triangle
+    double *Y = sd + R * R;  // R x R: L^-1 (lower triangle)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double s_wmax[kSolveThreads / 32];
+    __shared__ int s_wbad[kSolveThreads / 32];
+    double dmax = 0.0;
+    int bad = 0;
+    for (int e = tid; e < R * R; e += nt) {
+        double v = 1.0;
+        for (int k = 0; k < gl.n; ++k) v *= gl.g[k][e];
+        A[e] = v;
+        Q[e] = v;  // copy kept for the eigen fallback
+        bad |= isfinite(v) ? 0 : 1;
+        if (e / R == e % R) dmax = fmax(dmax, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((tid & 31) == 0) {
+        s_wmax[tid >> 5] = dmax;
+        s_wbad[tid >> 5] = bad;
+    }
+    __syncthreads();
+    dmax = 0.0;
+    bad = 0;
+    for (int w = 0; w < nt / 32; ++w) {
+        dmax = fmax(dmax, s_wmax[w]);
+        bad |= s_wbad[w];
+    }
+    if (bad && tid == 0) atomicOr(flags + 1, 1);
+    bool ok = dmax > 0.0 && !bad;
+    double dprev = 0.0;  // pivot of the previous column
+    for (int j = 0; j < R && ok; ++j) {
+        const double d = A[j * R + j];
+        if (!(d > kRankTol * dmax)) {
+            ok = false;  // every thread reads the same pivot: a uniform decision
+            break;
+        }
+        if (j > 0) {  // column j-1 -> L
+            const double l = sqrt(dprev), inv = 1.0 / l;
+            for (int i = j + tid; i < R; i += nt) A[i * R + j - 1] *= inv;
+            if (tid == 0) A[(j - 1) * R + j - 1] = l;
+        }
+        const double inv_d = 1.0 / d;
+        const int m = R - j - 1;
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = j + 1 + e / m, k = j + 1 + e % m;
+            if (k <= i) A[i * R + k] -= A[i * R + j] * A[k * R + j] * inv_d;
+        }
+        dprev = d;
+        __syncthreads();
+    }
+    if (!ok) {
+        __syncthreads();
+        pinv_jacobi(R, V, Q, W, Wf, flags);
+        return;
+    }
+    {  // last column
+        const double l = sqrt(dprev);
+        if (tid == 0) A[(R - 1) * R + R - 1] = l;
+    }
+    __syncthreads();
+    // Y = L^-1: thread c walks column c down the rows
+    for (int c = tid; c < R; c += nt) {
+        for (int i = 0; i < c; ++i) Y[i * R + c] = 0.0;
+        Y[c * R + c] = 1.0 / A[c * R + c];
+        for (int i = c + 1; i < R; ++i) {
+            double s0 = 0.0, s1 = 0.0;
+            int k = c;
+            for (; k + 1 < i; k += 2) {
+                s0 = fma(A[i * R + k], Y[k * R + c], s0);
+                s1 = fma(A[i * R + k + 1], Y[(k + 1) * R + c], s1);
+            }
+            if (k < i) s0 = fma(A[i * R + k], Y[k * R + c], s0);
+            Y[i * R + c] = -(s0 + s1) / A[i * R + i];
+        }
+    }
+    __syncthreads();
+    // W(a, b) = sum_{k >= max(a, b)} Y(k, a) Y(k, b), a <= b
+    const int ntri = R * (R + 1) / 2;
+    for (int t = tid; t < ntri; t += nt) {
+        int a = 0, rem = t;  // row a of the upper triangle holds R - a entries
+        while (rem >= R - a) {
+            rem -= R - a;
+            ++a;
+        }
+        const int b = a + rem;
+        double s0 = 0.0, s1 = 0.0;
+        int k = b;
+        for (; k + 1 < R; k += 2) {
+            s0 = fma(Y[k * R + a], Y[k * R + b], s0);
+            s1 = fma(Y[(k + 1) * R + a], Y[(k + 1) * R + b], s1);
+        }
+        if (k < R) s0 = fma(Y[k * R + a], Y[k * R + b], s0);
+        const double w = s0 + s1;
+        W[a * R + b] = w;
+        W[b * R + a] = w;
+        split_store(Wf, R * R, a * R + b, w);
+        split_store(Wf, R * R, b * R + a, w);
+    }
 }
 
 // ---------------------------------------------------------------- I x R kernels
@@ -485,7 +613,13 @@ int mode_update(const fcoo_t *X, cp_state_t *st, int n, bool last, cudaStream_t 
     memset(&gl, 0, sizeof(gl));
     for (int k = 0; k < st->nmodes; ++k)
         if (k != n) gl.g[gl.n++] = st->gram[k];
-    k_solve<<<1, kSolveThreads, 0, s>>>(gl, R, st->V, st->Q, st->W, st->Wf, st->flags);
+    if (R <= kSolveSmemMaxR) {
+        const int smem = 2 * R * R * 8;
+        FCOO_CUDA(cudaFuncSetAttribute(k_solve_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_solve_smem<<<1, kSolveThreads, smem, s>>>(gl, R, st->V, st->Q, st->W, st->Wf, st->flags);
+    } else {
+        k_solve<<<1, kSolveThreads, 0, s>>>(gl, R, st->V, st->Q, st->W, st->Wf, st->flags);
+    }
     FCOO_CUDA(cudaGetLastError());
     // Fu = M W, column norms
     const int nb = (int)ceil_div(I, kRowsPerBlock);
