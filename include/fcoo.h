@@ -328,7 +328,12 @@ int cp_state_load(cp_state_t *st, const void *blob, int64_t size, fcoo_stream_t 
  *                       * prod_{m != mode, k} F_m(idx_m(p), :)     (k != mode)
  *   dvals(p) = sum_r gradM(idx_mode(p), r) prod_{k != mode} F_k(idx_k(p), r)
  *   Xn: N handles as above (Xn[k] is used for dfactors[k]); dvals uses Xn[mode].
- * All outputs are fully overwritten.  Asynchronous on `stream`. */
+ * All outputs are fully overwritten.  Asynchronous on `stream`.
+ * Kind 0 with two or more gradients computes e once, on the first requested
+ * mode, and reuses it for the others.  For that it keeps, allocated on first
+ * use and freed by fcoo_destroy, 12 bytes per padded nonzero with the handle
+ * of the first requested mode and a 4-byte position map per padded nonzero
+ * with each other handle; calls that share handles must not overlap. */
 int spmttkrp_backward(const fcoo_t *const *Xn, const void *const *factors, int dtype, int R, const float *gradM,
                       int kind, int mode, float *const *dfactors, float *dvals, double *loss, fcoo_stream_t stream);
 

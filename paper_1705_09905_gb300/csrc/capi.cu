@@ -133,6 +133,8 @@ int fcoo_destroy(fcoo_t *X) {
     if (!X) return FCOO_OK;
     cudaDeviceSynchronize();
     dev_free(X->segkeys);
+    dev_free(X->grad_scratch);
+    dev_free(X->gmap);
     dev_free(X->base);
     free(X);
     return FCOO_OK;

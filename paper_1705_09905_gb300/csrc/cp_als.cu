@@ -424,7 +424,7 @@ __global__ void k_apply(const float *M, const float *Wf, int64_t I, int R, float
     // blockDim.x is a multiple of R: thread (r0, c) handles column c of rows r0, r0 + step, ...
     const int c = threadIdx.x % R, r0 = threadIdx.x / R, step = blockDim.x / R;
     __shared__ double red[1024];
-    double sq = 0.0;
+    Dot2 sq;  // compensated FP32: a long FP64 chain is slow at GB300's FP64 rate
     for (int r = r0; r < rows; r += step) {
         Dot2 d;
         for (int k = 0; k < R; ++k) {
@@ -434,9 +434,9 @@ __global__ void k_apply(const float *M, const float *Wf, int64_t I, int R, float
         }
         const float s = __fadd_rn(d.s, d.c);
         Fu[(i0 + r) * R + c] = s;
-        sq += (double)s * s;
+        sq.add(s, s);
     }
-    red[r0 * R + c] = sq;
+    red[r0 * R + c] = (double)sq.s + (double)sq.c;
     __syncthreads();
     if (r0 == 0) {
         double t = 0.0;
@@ -445,12 +445,33 @@ __global__ void k_apply(const float *M, const float *Wf, int64_t I, int R, float
     }
 }
 
-// lambda_c = sqrt(sum_b part[b][c]); one CTA.
-__global__ void k_lambda(const double *part, int nb, int R, double *lambda, int *flags) {
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+// sum_b part[b * stride + x] for the x this thread serves, over the blocks
+// b = q, q + P, ... ; the P partial sums of each x are then added in q order
+// by part_combine.  Short FP64 chains: GB300 runs FP64 at a small fraction of
+// its FP32 rate, and a 200-long dependent chain per thread is its latency
+// times 200.
+__device__ __forceinline__ double part_sum(const double *part, int nb, int64_t stride, int x, int q, int P) {
+    double s0 = 0.0, s1 = 0.0;
+    int b = q;
+    for (; b + P < nb; b += 2 * P) {
+        s0 += part[(int64_t)b * stride + x];
+        s1 += part[(int64_t)(b + P) * stride + x];
+    }
+    if (b < nb) s0 += part[(int64_t)b * stride + x];
+    return s0 + s1;
+}
+
+// lambda_c = sqrt(sum_b part[b][c]); one CTA of kSolveThreads threads, R <= 128.
+__global__ void __launch_bounds__(kSolveThreads) k_lambda(const double *part, int nb, int R, double *lambda,
+                                                          int *flags) {
+    __shared__ double red[kSolveThreads];
+    const int P = blockDim.x / R, q = threadIdx.x / R, c = threadIdx.x % R;
+    if (q < P) red[threadIdx.x] = part_sum(part, nb, R, c, q, P);
+    __syncthreads();
+    if (threadIdx.x < R) {
         double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part[(int64_t)b * R + c];
-        double l = sqrt(s);
+        for (int t = 0; t < P; ++t) s += red[t * R + c];
+        const double l = sqrt(s);
         if (!isfinite(l)) atomicOr(flags + 1, 1);
         lambda[c] = l;
     }
@@ -467,7 +488,7 @@ __global__ void k_normalize(const float *Fu, const double *lambda, int64_t I, in
     const int c = threadIdx.x % R, r0 = threadIdx.x / R, step = blockDim.x / R;
     const double l = lambda[c];
     const float inv = l > 0.0 ? (float)(1.0 / l) : 1.0f;
-    double dot = 0.0;
+    Dot2 dot;
     for (int r = r0; r < rows; r += step) {
         const int64_t e = (i0 + r) * R + c;
         float v = Fu[e] * inv;
@@ -475,10 +496,10 @@ __global__ void k_normalize(const float *Fu, const double *lambda, int64_t I, in
         if constexpr (sizeof(TF) == 2) st = __float2bfloat16_rn(v);
         else st = v;
         F[e] = st;
-        if (dotpart) dot += (double)M[e] * (double)ldf<TF>(&st);
+        if (dotpart) dot.add(M[e], ldf<TF>(&st));
     }
     if (dotpart) {
-        red[r0 * R + c] = dot;
+        red[r0 * R + c] = (double)dot.s + (double)dot.c;
         __syncthreads();
         if (r0 == 0) {
             double t = 0.0;
@@ -499,20 +520,42 @@ __global__ void k_gram_part(const TF *F, int64_t I, int R, double *part) {
     const int rows = (int)min((int64_t)kRowsPerBlock, I - i0);
     for (int e = threadIdx.x; e < rows * R; e += blockDim.x) sF[e] = ldf<TF>(F + i0 * R + e);
     __syncthreads();
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-        const int a = e / R, b = e % R;
-        Dot2 d;
-        for (int r = 0; r < rows; ++r) d.add(sF[r * R + a], sF[r * R + b]);
-        part[(int64_t)blockIdx.x * R * R + e] = (double)d.s + (double)d.c;
+    // four entries per pass: four independent compensated chains in flight
+    const int RR = R * R, nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < RR; e0 += 4 * nt) {
+        int a[4], b[4];
+        Dot2 d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = min(e0 + u * nt, RR - 1);
+            a[u] = e / R;
+            b[u] = e % R;
+        }
+        for (int r = 0; r < rows; ++r) {
+            const float *row = sF + r * R;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) d[u].add(row[a[u]], row[b[u]]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * nt;
+            if (e < RR) part[(int64_t)blockIdx.x * RR + e] = (double)d[u].s + (double)d[u].c;
+        }
     }
 }
 
-__global__ void k_gram_reduce(const double *part, int nb, int R, double *G) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= R * R) return;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * R * R + e];
-    G[e] = s;
+// G[e] = sum_b part[b][e]; blocks of 256 threads serve 32 entries, 8 threads each.
+__global__ void __launch_bounds__(256) k_gram_reduce(const double *part, int nb, int R, double *G) {
+    __shared__ double red[256];
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), q = threadIdx.x >> 5;
+    const int RR = R * R;
+    red[threadIdx.x] = x < RR ? part_sum(part, nb, RR, x, q, 8) : 0.0;
+    __syncthreads();
+    if (threadIdx.x < 32 && x < RR) {
+        double s = 0.0;
+        for (int t = 0; t < 8; ++t) s += red[t * 32 + threadIdx.x];
+        G[x] = s;
+    }
 }
 
 struct GramAll {
@@ -529,10 +572,9 @@ __global__ void k_fit(GramAll ga, const double *lambda, int R, const double *dot
         for (int k = 0; k < ga.n; ++k) v *= ga.g[k][e];
         xh += v;
     }
-    for (int c = threadIdx.x; c < R; c += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += dotpart[(int64_t)b * R + c];
-        inner += lambda[c] * s;
+    {
+        const int P = blockDim.x / R, q = threadIdx.x / R, c = threadIdx.x % R;
+        if (q < P) inner = lambda[c] * part_sum(dotpart, nb, R, c, q, P);
     }
     red[threadIdx.x] = xh;
     __syncthreads();
@@ -586,7 +628,7 @@ int gram_of(cp_state_t *st, int k, cudaStream_t s) {
         k_gram_part<float><<<nb, 256, smem, s>>>((const float *)st->F[k], I, R, st->part);
     }
     FCOO_CUDA(cudaGetLastError());
-    k_gram_reduce<<<(unsigned)ceil_div(R * R, 256), 256, 0, s>>>(st->part, nb, R, st->gram[k]);
+    k_gram_reduce<<<(unsigned)ceil_div(R * R, 32), 256, 0, s>>>(st->part, nb, R, st->gram[k]);
     FCOO_CUDA(cudaGetLastError());
     return FCOO_OK;
 }

@@ -17,6 +17,8 @@
 
 #include <vector>
 
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace fcx {
@@ -407,6 +409,10 @@ extern "C" int fcoo_build(int nmodes, const uint32_t *dims, int64_t nnz, const u
     }
     cudaGetDevice(&X->device);
     X->max_grid = num_sms() * kMaxCtasPerSm;
+    {
+        static std::atomic<uint64_t> next_uid{1};
+        X->uid = next_uid.fetch_add(1);
+    }
 
     const int64_t n = nnz, npad = X->npad;
     const int64_t nwords = npad / 32;

@@ -70,6 +70,15 @@ struct fcoo {
     unsigned int *counter;
     double *red_part;  // max_grid per-CTA partial sums (loss)
     int max_grid;
+    // sparse-fit gradient scratch, allocated on first use.  On the handle the
+    // residuals are computed on: e in its F-COO order, one other mode's copy
+    // of e, and an inverse permutation (npad entries each).  On the other
+    // handles: gmap[p] = position in the source handle's order of nonzero p,
+    // valid for the handle whose uid is gmap_src.
+    float *grad_scratch;
+    uint32_t *gmap;
+    uint64_t gmap_src;
+    uint64_t uid;  // unique per handle built in this process
     int64_t bytes_val, bytes_pidx, bytes_bf, bytes_sf, bytes_segmap, bytes_aux, bytes_scratch;
 };
 
@@ -92,6 +101,7 @@ struct StreamParams {
     const void *T;            // target rows (dtype of F), row = output row of the segment
     const uint32_t *perm;     // F-COO position -> original COO position
     float *dvals;             // dvals[perm[p]] = dsign * e, or NULL
+    int dvals_fcoo;           // 1: dvals[p] (F-COO order) instead of dvals[perm[p]]
     float dsign;
     int sub_val;
     double *loss_part;        // per-CTA sum of e^2, or NULL

@@ -3,17 +3,23 @@
 // kind 0, sparse CP fit over the observed entries:
 //   e(p) = sum_r prod_k F_k(idx_k(p), r) - x(p),  loss = 1/2 sum e(p)^2
 //   dF_n(i,:) = sum_{p: idx_n(p) = i} e(p) prod_{k != n} F_k(idx_k(p), :)
-// Each dF_n is one pass of the streaming kernel over the mode-n F-COO copy
-// with residual weights: the segment's own row F_n(i,:) is loaded once per
-// segment, e(p) is a group-wide dot product per nonzero, and e(p) times the
-// Hadamard product of the gathered rows is reduced per segment exactly like
-// SpMTTKRP.  The first pass also writes the loss partials and dvals = -e
-// (scattered to the caller's COO order through the handle's permutation).
+// The first requested dF_n is one pass of the streaming kernel over the
+// mode-n F-COO copy with residual weights: the segment's own row F_n(i,:) is
+// loaded once per segment, e(p) is a group-wide dot product per nonzero, and
+// e(p) times the Hadamard product of the gathered rows is reduced per segment
+// exactly like SpMTTKRP.  The same pass writes the loss partials and e itself,
+// in its own F-COO order (sequential stores).  Every other dF_m is then a
+// plain SpMTTKRP of the mode-m copy whose value stream is e gathered into
+// mode-m order through a position map built once per pair of handles (e is
+// the same for every mode): one 4-byte gather per nonzero instead of
+// recomputing the dot product.
 // kind 1, adjoint of M = SpMTTKRP_mode(X, F) for a cotangent G = dL/dM:
 //   dF_k = SpMTTKRP_k(X, F with F_mode := G)        (plain value-weighted pass)
 //   dval(p) = <G(idx_mode(p), :), prod_{k != mode} F_k(idx_k(p), :)>
 //                                                   (residual pass, no output rows)
 #include <string.h>
+
+#include <algorithm>
 
 #include "internal.cuh"
 
@@ -31,6 +37,39 @@ __global__ void k_half_sum(const double *part, int n, double *out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = 0.5 * red[0];
+}
+
+// w[p] = e[map[p]] for p < nnz, four independent loads in flight per thread
+__global__ void k_gather_vals(const float *e, const uint32_t *map, int64_t nnz, float *w) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; p + 3 * stride < nnz; p += 4 * stride) {
+        uint32_t m[4];
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m[u] = __ldg(map + p + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldg(e + m[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[p + u * stride] = v[u];
+    }
+    for (; p < nnz; p += stride) w[p] = __ldg(e + __ldg(map + p));
+}
+
+// inv[perm[p]] = p for p < nnz (the caller's COO position -> F-COO position)
+__global__ void k_invert_perm(const uint32_t *perm, int64_t nnz, uint32_t *inv) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[p]] = (uint32_t)p;
+}
+
+// out[perm[p]] = sign * in[p] for p < nnz
+__global__ void k_scatter_scaled(const float *in, const uint32_t *perm, int64_t nnz, float sign, float *out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        out[perm[p]] = sign * in[p];
+}
+
+unsigned grid_for(int64_t n) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8 * 1024));
 }
 
 int check_handles(const fcoo_t *const *Xn, int &nmodes, const char *who) {
@@ -51,7 +90,8 @@ int check_handles(const fcoo_t *const *Xn, int &nmodes, const char *who) {
 // Residual-weighted pass over handle X: target rows T, product rows from
 // `factors` (indexed by mode), optional output rows, loss partials, dvals.
 int residual_pass(const fcoo_t *X, const void *const *factors, const void *T, int dtype, int R, float *out,
-                  bool with_loss, float *dvals, float dsign, int sub_val, cudaStream_t s, int *grid) {
+                  bool with_loss, float *dvals, float dsign, int sub_val, cudaStream_t s, int *grid,
+                  int dvals_fcoo = 0) {
     StreamParams p;
     stream_params_from(X, p);
     for (int m = 0; m < X->nprod; ++m) p.F[m] = factors[X->prod_modes[m]];
@@ -60,6 +100,7 @@ int residual_pass(const fcoo_t *X, const void *const *factors, const void *T, in
     p.out_rows = X->dims[X->mode];
     p.T = T;
     p.dvals = dvals;
+    p.dvals_fcoo = dvals_fcoo;
     p.dsign = dsign;
     p.sub_val = sub_val;
     p.loss_part = with_loss ? X->red_part : nullptr;
@@ -98,18 +139,68 @@ extern "C" int spmttkrp_backward(const fcoo_t *const *Xn, const void *const *fac
         bool first = true;
         int loss_grid = 0;
         const fcoo_t *loss_X = nullptr;
+        int nwant = 0;
+        for (int n = 0; n < nmodes; ++n) nwant += (dfactors && dfactors[n]) ? 1 : 0;
+        float *ebuf = nullptr, *wbuf = nullptr;
         for (int n = 0; n < nmodes; ++n) {
             float *out = dfactors ? dfactors[n] : nullptr;
             if (!out) continue;
-            int grid = 0;
-            rc = residual_pass(Xn[n], factors, factors[n], dtype, R, out, first && loss, first ? dvals : nullptr,
-                               -1.0f, 1, s, &grid);
-            if (rc) return rc;
             if (first) {
+                int grid = 0;
+                if (nwant > 1) {
+                    // e in this handle's F-COO order, kept for the other modes
+                    fcoo_t *Xs = const_cast<fcoo_t *>(Xn[n]);
+                    if (!Xs->grad_scratch) {
+                        void *q = nullptr;
+                        FCOO_CUDA(dev_alloc(&q, (size_t)Xs->npad * 12));
+                        Xs->grad_scratch = (float *)q;
+                        FCOO_CUDA(cudaMemsetAsync(q, 0, (size_t)Xs->npad * 12, s));
+                    }
+                    ebuf = Xs->grad_scratch;
+                    wbuf = ebuf + Xs->npad;
+                    rc = residual_pass(Xs, factors, factors[n], dtype, R, out, loss != nullptr, ebuf, 1.0f, 1, s,
+                                       &grid, 1);
+                } else {
+                    rc = residual_pass(Xn[n], factors, factors[n], dtype, R, out, loss != nullptr, dvals, -1.0f, 1,
+                                       s, &grid);
+                }
+                if (rc) return rc;
                 loss_grid = grid;
                 loss_X = Xn[n];
+                first = false;
+                continue;
             }
-            first = false;
+            // dF_n = SpMTTKRP_n with the values e gathered into mode-n order
+            fcoo_t *Xm = const_cast<fcoo_t *>(Xn[n]);
+            if (!Xm->gmap || Xm->gmap_src != loss_X->uid) {
+                if (!Xm->gmap) {
+                    void *q = nullptr;
+                    FCOO_CUDA(dev_alloc(&q, (size_t)Xm->npad * 4));
+                    Xm->gmap = (uint32_t *)q;
+                }
+                uint32_t *inv = reinterpret_cast<uint32_t *>(ebuf + 2 * loss_X->npad);
+                k_invert_perm<<<grid_for(nnz), 256, 0, s>>>(loss_X->perm, nnz, inv);
+                FCOO_CUDA(cudaGetLastError());
+                k_gather_vals<<<grid_for(nnz), 256, 0, s>>>(reinterpret_cast<const float *>(inv), Xm->perm, nnz,
+                                                            reinterpret_cast<float *>(Xm->gmap));
+                FCOO_CUDA(cudaGetLastError());
+                Xm->gmap_src = loss_X->uid;
+            }
+            k_gather_vals<<<grid_for(nnz), 256, 0, s>>>(ebuf, Xm->gmap, nnz, wbuf);
+            FCOO_CUDA(cudaGetLastError());
+            StreamParams p;
+            stream_params_from(Xm, p);
+            for (int m = 0; m < Xm->nprod; ++m) p.F[m] = factors[Xm->prod_modes[m]];
+            p.val = wbuf;
+            p.out = out;
+            p.R = R;
+            p.out_rows = Xm->dims[n];
+            rc = launch_stream_kernel(p, dtype, s, 0);
+            if (rc) return rc;
+        }
+        if (ebuf && dvals) {
+            k_scatter_scaled<<<grid_for(nnz), 256, 0, s>>>(ebuf, loss_X->perm, nnz, -1.0f, dvals);
+            FCOO_CUDA(cudaGetLastError());
         }
         if (first && (loss || dvals)) {  // no gradient asked for: one loss / dvals pass
             rc = residual_pass(Xn[0], factors, factors[0], dtype, R, nullptr, loss != nullptr, dvals, -1.0f, 1, s,

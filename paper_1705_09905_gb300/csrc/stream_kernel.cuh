@@ -300,7 +300,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
     constexpr int G = kThreads / LPR;  // groups per CTA
     constexpr int RT = NCH * LPR * E;  // columns covered by a group
     const int nprod = NP > 0 ? NP : p.nprod;
-    const int nstream = nprod + 1;
+    // stage layout: the product-mode index streams, the values and, for the
+    // residual kind, the permutation to the caller's COO order (for dvals)
+    const int nstream = nprod + 1 + (KIND == 1 ? 1 : 0);
     const int R = p.R;
     const int tid = threadIdx.x, lane = tid & 31;
     const int g = tid / LPR, lig = tid % LPR;
@@ -367,18 +369,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                 if constexpr (NP > 0 && LPR <= CPA) {
                     // piece i * LPR + lig: the array is the same for every lane
 #pragma unroll
-                    for (int i = 0; i < (NP + 1) * CPA / LPR; ++i) {
+                    for (int i = 0; i < (NP + 1 + (KIND == 1 ? 1 : 0)) * CPA / LPR; ++i) {
                         const int a = i * LPR / CPA, q = i * LPR % CPA + lig;
-                        const void *src = a < NP ? (const void *)(p.pidx[a] + base + q * 4)
-                                                 : (const void *)(p.val + base + q * 4);
+                        if (a == NP + 1 && (!p.dvals || p.dvals_fcoo)) continue;
+                        const void *src = a < NP    ? (const void *)(p.pidx[a] + base + q * 4)
+                                          : a == NP ? (const void *)(p.val + base + q * 4)
+                                                    : (const void *)(p.perm + base + q * 4);
                         cp_async16(slot + a * T * 4 + q * 16, src);
                     }
                 } else {
                     const int nchunks = nstream * CPA;
                     for (int c = lig; c < nchunks; c += LPR) {
                         const int a = c / CPA, q = c % CPA;
-                        const void *src = a < nprod ? (const void *)(p.pidx[a] + base + q * 4)
-                                                    : (const void *)(p.val + base + q * 4);
+                        if (a == nprod + 1 && (!p.dvals || p.dvals_fcoo)) continue;
+                        const void *src = a < nprod    ? (const void *)(p.pidx[a] + base + q * 4)
+                                          : a == nprod ? (const void *)(p.val + base + q * 4)
+                                                       : (const void *)(p.perm + base + q * 4);
                         cp_async16(slot + a * T * 4 + q * 16, src);
                     }
                 }
@@ -536,7 +542,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
         };
         // acc_st += w * (brow * row), w = val (KIND 0) or the residual weight
         // (KIND 1); element pairs go through the paired FP32 instructions
-        auto accumulate = [&](float v, const raw (&cr)[NCH], int64_t pos) {
+        // (u = position in the stage that starts at nonzero `base`)
+        auto accumulate = [&](float v, const raw (&cr)[NCH], const unsigned char *slot, int64_t base, int u) {
             float t[NCH][E];
 #pragma unroll
             for (int c = 0; c < NCH; ++c) IO::cvt(cr[c], t[c]);
@@ -574,7 +581,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                 const float w = p.sub_val ? d - v : d;
                 if (lig == 0) {
                     lsum = fmaf(w, w, lsum);
-                    if (p.dvals) p.dvals[__ldg(p.perm + pos)] = p.dsign * w;
+                    if (p.dvals) {
+                        // in F-COO order, or the caller's COO order through the streamed permutation
+                        const int64_t at = p.dvals_fcoo ? base + u
+                                                        : (int64_t)reinterpret_cast<const uint32_t *>(
+                                                              slot + (nprod + 1) * T * 4)[u];
+                        p.dvals[at] = p.dsign * w;
+                    }
                 }
 #pragma unroll
                 for (int c = 0; c < NCH; ++c)
@@ -702,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                     } else if constexpr (NP != 1) {
                         if (f) set_brow_sync(slot, qt * Q + q);
                     }
-                    accumulate(b.vv[q], b.cr[q], base + qt * Q + q);
+                    accumulate(b.vv[q], b.cr[q], slot, base, qt * Q + q);
                 }
             } else if (NP == 1 && KIND == 0 && !p.segrow && has_out) {
                 // SpTTM: fibres of one or two nonzeros are the norm, so segment
@@ -726,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                         row += hd;
                         orow += hd ? R : 0;
                     }
-                    accumulate(b.vv[q], b.cr[q], base + qt * Q + q);
+                    accumulate(b.vv[q], b.cr[q], slot, base, qt * Q + q);
                 }
             } else {
 #pragma unroll
@@ -740,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                             set_brow_sync(slot, qt * Q + q);
                         }
                     }
-                    accumulate(b.vv[q], b.cr[q], base + qt * Q + q);
+                    accumulate(b.vv[q], b.cr[q], slot, base, qt * Q + q);
                 }
             }
         };
@@ -776,7 +789,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
                         set_brow_sync(slot, u);
                     }
                 }
-                accumulate(sv[u], cr, base + u);
+                accumulate(sv[u], cr, slot, base, u);
             }
         };
 
@@ -951,7 +964,7 @@ int launch_variant(StreamParams &p, cudaStream_t s) {
     constexpr int G = kThreads / LPR;
     constexpr int RT = NCH * LPR * E;
     auto kern = k_stream<TF, E, LPR, NCH, NP, KIND>;
-    const size_t smem = stream_smem_bytes(p.nprod + 1, G, RT);
+    const size_t smem = stream_smem_bytes(p.nprod + 1 + (KIND == 1 ? 1 : 0), G, RT);
     static size_t cached_smem = 0;
     static int cached_occ = 0;
     if (cached_smem != smem) {
