@@ -306,19 +306,22 @@ def _handles(Xn):
     return ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)), arr
 
 
-def sparse_fit_grad(Xn: Sequence[FCOO], factors: Sequence[torch.Tensor], want_dvals: bool = False, stream=None):
-    """Loss 1/2 sum_obs (model - x)^2 and its gradients w.r.t. every factor
-    (and the values, in the caller's COO order) -- kind 0 of spmttkrp_backward."""
+def sparse_fit_grad(Xn: Sequence[FCOO], factors: Sequence[torch.Tensor], want_dvals: bool = False, stream=None,
+                    modes: Optional[Sequence[int]] = None):
+    """Loss 1/2 sum_obs (model - x)^2 and its gradients w.r.t. the factors of
+    ``modes`` (default: every factor; the others are None) and the values, in
+    the caller's COO order -- kind 0 of spmttkrp_backward."""
     dims = Xn[0].dims
     R = int(factors[0].shape[1])
     ptrs, dt = _factor_ptrs(factors, dims, R)
     dev = factors[0].device
-    grads = [torch.empty((d, R), dtype=torch.float32, device=dev) for d in dims]
+    want = set(range(len(dims)) if modes is None else (int(m) for m in modes))
+    grads = [torch.empty((d, R), dtype=torch.float32, device=dev) if n in want else None for n, d in enumerate(dims)]
     dvals = torch.empty(Xn[0].nnz, dtype=torch.float32, device=dev) if want_dvals else None
     loss = torch.empty((), dtype=torch.float64, device=dev)
     hp, _k1 = _handles(Xn)
     fp, _k2 = ptr_array(ptrs)
-    gp, _k3 = ptr_array([g.data_ptr() for g in grads])
+    gp, _k3 = ptr_array([g.data_ptr() if g is not None else None for g in grads])
     check(lib.spmttkrp_backward(hp, fp, dt, R, None, 0, 0, gp, dvals.data_ptr() if dvals is not None else None,
                                 loss.data_ptr(), _stream(stream)))
     return loss, grads, dvals
