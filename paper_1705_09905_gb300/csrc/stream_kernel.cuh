@@ -293,8 +293,22 @@ __device__ __forceinline__ void zero_rows(float *out, int R, int lig, int64_t fr
 // (columns of lane l, chunk c: (c * LPR + l) * E ... + E - 1); NP: number of
 // product modes (0: runtime value p.nprod); KIND: 0 = value weights
 // (SpMTTKRP / SpTTM), 1 = residual weights.
+// Resident CTAs per SM the register budget is set for: 3 (80 registers) for
+// the one-product value pass with at most four columns per lane (SpTTM at
+// R <= 16: short segments, two-nonzero quarters; measured 9 % faster with 24
+// warps per SM than with 16), 2 (128 registers) for the others, whose row
+// buffers need them.
+template <int E, int NCH, int NP, int KIND>
+constexpr bool stream_three_ctas() {
+    return NP == 1 && KIND == 0 && E * NCH <= 4;
+}
+template <int E, int NCH, int NP, int KIND>
+constexpr int stream_min_blocks() {
+    return stream_three_ctas<E, NCH, NP, KIND>() ? 3 : 2;
+}
+
 template <typename TF, int E, int LPR, int NCH, int NP, int KIND>
-__global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
+__global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>()) k_stream(const StreamParams p) {
     using IO = RowIO<TF, E>;
     using raw = typename IO::raw;
     constexpr int G = kThreads / LPR;  // groups per CTA
@@ -628,12 +642,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream(const StreamParams p) {
         }
 
         // ---- software pipeline over quarters of a stage (Q nonzeros; 4, or 2
-        // when a lane holds more than 4 columns): the gathers of quarter h+1
+        // when a lane holds more than 4 columns or the variant runs 3 CTAs per
+        // SM): the gathers of quarter h+1
         // are in flight while quarter h is consumed.  A full stage is walked
         // by a rolled loop over pairs of quarters (two register buffers); the
         // first quarter of the next stage is requested while the last quarter
         // of the current one is consumed.
-        constexpr int Q = E * NCH <= 4 ? 4 : 2;
+        constexpr int Q = (E * NCH <= 4 && !stream_three_ctas<E, NCH, NP, KIND>()) ? 4 : 2;
         constexpr int QPS = T / Q;  // quarters per stage (even)
         static_assert(QPS % 2 == 0, "quarters are consumed in pairs");
         // the unrolled pipeline serves the 3-way SpMTTKRP and SpTTM vector
