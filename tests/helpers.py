@@ -2,7 +2,7 @@
 import numpy as np
 import torch
 
-# spec tolerance for FP32 paths: relative Frobenius error vs the FP64 oracle
+# tolerance for FP32 paths: relative Frobenius error vs the FP64 oracle
 REL_FRO = 1e-5
 # element-wise: error relative to the sum of absolute terms of that element
 REL_ABS = 2e-5
