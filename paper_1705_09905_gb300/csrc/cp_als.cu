@@ -272,10 +272,11 @@ constexpr int kSolveSmemMaxR = 112;
 // The same solve with the matrices in shared memory (R <= kSolveSmemMaxR),
 // for the FP64 rate of GB300 and to keep each step off the memory system:
 //  * V = Hadamard of the Grams; max diag(V) and finiteness by block reduction;
-//  * right-looking Cholesky with one barrier per column: step j updates the
-//    trailing triangle with the unscaled column, A(i,k) -= A(i,j) A(k,j) / d_j
-//    (= l_ij l_kj), and scales column j-1 to L in the same phase;
-//  * Y = L^-1 column by column (one thread per column, no barrier);
+//  * right-looking Cholesky, three barriers per column: the pivot's square
+//    root and reciprocal by one thread, the column scaled to L, the trailing
+//    lower triangle updated with one FMA per entry;
+//  * Y = L^-1 column by column (one thread per column, no barrier, the
+//    diagonal reciprocals reused);
 //  * W = Y^T Y on the upper triangle, mirrored, and split to FP32 hi + lo.
 // A non-positive pivot d_j <= kRankTol * max diag(V) (or a non-finite V) sends
 // the whole CTA to the Jacobi pseudo-inverse, as in k_solve.
@@ -313,42 +314,46 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_smem(GramList gl, int R
         bad |= s_wbad[w];
     }
     if (bad && tid == 0) atomicOr(flags + 1, 1);
-    bool ok = dmax > 0.0 && !bad;
-    double dprev = 0.0;  // pivot of the previous column
-    for (int j = 0; j < R && ok; ++j) {
-        const double d = A[j * R + j];
-        if (!(d > kRankTol * dmax)) {
-            ok = false;  // every thread reads the same pivot: a uniform decision
-            break;
+    __shared__ double s_inv[kSolveSmemMaxR];  // 1 / L(j, j)
+    __shared__ int s_ok;
+    if (tid == 0) s_ok = (dmax > 0.0 && !bad) ? 1 : 0;
+    __syncthreads();
+    // Right-looking Cholesky.  Per column j: thread 0 takes the pivot (the one
+    // square root and division of the step: at GB300's FP64 rate, a division
+    // in every thread would cost more than the update), the column is scaled,
+    // and the trailing lower triangle is updated row by row (a warp per row,
+    // its lanes along the row), one FMA per entry.
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    for (int j = 0; j < R; ++j) {
+        if (tid == 0) {
+            const double d = A[j * R + j];
+            if (!(d > kRankTol * dmax)) {
+                s_ok = 0;
+            } else {
+                const double l = sqrt(d);
+                A[j * R + j] = l;
+                s_inv[j] = 1.0 / l;
+            }
         }
-        if (j > 0) {  // column j-1 -> L
-            const double l = sqrt(dprev), inv = 1.0 / l;
-            for (int i = j + tid; i < R; i += nt) A[i * R + j - 1] *= inv;
-            if (tid == 0) A[(j - 1) * R + j - 1] = l;
+        __syncthreads();
+        if (!s_ok) break;  // uniform: read after the barrier
+        const double inv = s_inv[j];
+        for (int i = j + 1 + tid; i < R; i += nt) A[i * R + j] *= inv;
+        __syncthreads();
+        for (int i = j + 1 + warp; i < R; i += nwarps) {
+            const double lij = A[i * R + j];
+            for (int k = j + 1 + lane; k <= i; k += 32) A[i * R + k] = fma(-lij, A[k * R + j], A[i * R + k]);
         }
-        const double inv_d = 1.0 / d;
-        const int m = R - j - 1;
-        for (int e = tid; e < m * m; e += nt) {
-            const int i = j + 1 + e / m, k = j + 1 + e % m;
-            if (k <= i) A[i * R + k] -= A[i * R + j] * A[k * R + j] * inv_d;
-        }
-        dprev = d;
         __syncthreads();
     }
-    if (!ok) {
-        __syncthreads();
+    if (!s_ok) {
         pinv_jacobi(R, V, Q, W, Wf, flags);
         return;
     }
-    {  // last column
-        const double l = sqrt(dprev);
-        if (tid == 0) A[(R - 1) * R + R - 1] = l;
-    }
-    __syncthreads();
-    // Y = L^-1: thread c walks column c down the rows
+    // Y = L^-1: thread c walks column c down the rows (1 / L(i, i) from s_inv)
     for (int c = tid; c < R; c += nt) {
         for (int i = 0; i < c; ++i) Y[i * R + c] = 0.0;
-        Y[c * R + c] = 1.0 / A[c * R + c];
+        Y[c * R + c] = s_inv[c];
         for (int i = c + 1; i < R; ++i) {
             double s0 = 0.0, s1 = 0.0;
             int k = c;
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_smem(GramList gl, int R
                 s1 = fma(A[i * R + k + 1], Y[(k + 1) * R + c], s1);
             }
             if (k < i) s0 = fma(A[i * R + k], Y[k * R + c], s0);
-            Y[i * R + c] = -(s0 + s1) / A[i * R + i];
+            Y[i * R + c] = -(s0 + s1) * s_inv[i];
         }
     }
     __syncthreads();
