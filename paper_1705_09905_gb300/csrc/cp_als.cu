@@ -272,11 +272,11 @@ constexpr int kSolveSmemMaxR = 112;
 // The same solve with the matrices in shared memory (R <= kSolveSmemMaxR),
 // for the FP64 rate of GB300 and to keep each step off the memory system:
 //  * V = Hadamard of the Grams; max diag(V) and finiteness by block reduction;
-//  * right-looking Cholesky, three barriers per column: the pivot's square
-//    root and reciprocal by one thread, the column scaled to L, the trailing
-//    lower triangle updated with one FMA per entry;
-//  * Y = L^-1 column by column (one thread per column, no barrier, the
-//    diagonal reciprocals reused);
+//  * right-looking Cholesky, two barriers per column: the pivot's reciprocal
+//    square root by one thread, then one FMA per trailing entry (the column
+//    is scaled to L a step later);
+//  * Y = L^-1 by forward substitution over all columns at once, one barrier
+//    per row;
 //  * W = Y^T Y on the upper triangle, mirrored, and split to FP32 hi + lo.
 // A non-positive pivot d_j <= kRankTol * max diag(V) (or a non-finite V) sends
 // the whole CTA to the Jacobi pseudo-inverse, as in k_solve.
@@ -315,14 +315,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_smem(GramList gl, int R
     }
     if (bad && tid == 0) atomicOr(flags + 1, 1);
     __shared__ double s_inv[kSolveSmemMaxR];  // 1 / L(j, j)
+    __shared__ double s_inv2;
     __shared__ int s_ok;
     if (tid == 0) s_ok = (dmax > 0.0 && !bad) ? 1 : 0;
     __syncthreads();
-    // Right-looking Cholesky.  Per column j: thread 0 takes the pivot (the one
-    // square root and division of the step: at GB300's FP64 rate, a division
-    // in every thread would cost more than the update), the column is scaled,
-    // and the trailing lower triangle is updated row by row (a warp per row,
-    // its lanes along the row), one FMA per entry.
+    // Right-looking Cholesky, two barriers per column.  GB300 runs FP64 with a
+    // long latency per dependent operation, so the critical path is kept
+    // short: thread 0 takes the pivot with one reciprocal square root
+    // (l = d * r, 1 / l = r), and every trailing entry gets one FMA with the
+    // still unscaled column, A(i,k) -= (A(i,j) / d) A(k,j) = l_ij l_kj.
+    // Column j is scaled to L in the next column's update phase, when nothing
+    // reads it any more.
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     for (int j = 0; j < R; ++j) {
         if (tid == 0) {
@@ -330,19 +333,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_smem(GramList gl, int R
             if (!(d > kRankTol * dmax)) {
                 s_ok = 0;
             } else {
-                const double l = sqrt(d);
-                A[j * R + j] = l;
-                s_inv[j] = 1.0 / l;
+                const double r = rsqrt(d);
+                s_inv[j] = r;
+                s_inv2 = r * r;
             }
         }
         __syncthreads();
         if (!s_ok) break;  // uniform: read after the barrier
-        const double inv = s_inv[j];
-        for (int i = j + 1 + tid; i < R; i += nt) A[i * R + j] *= inv;
-        __syncthreads();
+        const double r2 = s_inv2;
+        if (j > 0) {  // column j-1 -> L
+            const double r = s_inv[j - 1];
+            for (int i = j + tid; i < R; i += nt) A[i * R + j - 1] *= r;
+        }
         for (int i = j + 1 + warp; i < R; i += nwarps) {
-            const double lij = A[i * R + j];
-            for (int k = j + 1 + lane; k <= i; k += 32) A[i * R + k] = fma(-lij, A[k * R + j], A[i * R + k]);
+            const double t = A[i * R + j] * r2;
+            for (int k = j + 1 + lane; k <= i; k += 32) A[i * R + k] = fma(-t, A[k * R + j], A[i * R + k]);
         }
         __syncthreads();
     }
@@ -350,21 +355,29 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_smem(GramList gl, int R
         pinv_jacobi(R, V, Q, W, Wf, flags);
         return;
     }
-    // Y = L^-1: thread c walks column c down the rows (1 / L(i, i) from s_inv)
-    for (int c = tid; c < R; c += nt) {
-        for (int i = 0; i < c; ++i) Y[i * R + c] = 0.0;
-        Y[c * R + c] = s_inv[c];
-        for (int i = c + 1; i < R; ++i) {
-            double s0 = 0.0, s1 = 0.0;
-            int k = c;
-            for (; k + 1 < i; k += 2) {
-                s0 = fma(A[i * R + k], Y[k * R + c], s0);
-                s1 = fma(A[i * R + k + 1], Y[(k + 1) * R + c], s1);
-            }
-            if (k < i) s0 = fma(A[i * R + k], Y[k * R + c], s0);
-            Y[i * R + c] = -(s0 + s1) * s_inv[i];
+    // the diagonal of L: l_jj = d_j * r_j (the last column has nothing below it)
+    for (int i = tid; i < R; i += nt) A[i * R + i] *= s_inv[i];
+    // Y = L^-1 by forward substitution, all columns at once and the rows in
+    // order: once row k of Y is final, every later row subtracts its multiple
+    // of it (one FMA per entry, independent across entries, a barrier per
+    // row) -- the dependent chain is R steps long instead of R^2 / 2.
+    // Y starts as the identity and holds the running right-hand sides.
+    for (int e = tid; e < R * R; e += nt) Y[e] = (e / R == e % R) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k < R; ++k) {
+        // row k - 1 is final: scale it by 1 / l_(k-1)(k-1)
+        if (k > 0)
+            for (int c = tid; c < k; c += nt) Y[(k - 1) * R + c] *= s_inv[k - 1];
+        // rows i > k, columns c <= k: Y(i, c) -= l_ik * Y(k, c) / l_kk
+        const int w = k + 1, m = R - k - 1;
+        const double rk = s_inv[k];
+        for (int e = tid; e < m * w; e += nt) {
+            const int i = k + 1 + e / w, c = e % w;
+            Y[i * R + c] = fma(-A[i * R + k] * rk, Y[k * R + c], Y[i * R + c]);
         }
+        __syncthreads();
     }
+    for (int c = tid; c < R; c += nt) Y[(R - 1) * R + c] *= s_inv[R - 1];
     __syncthreads();
     // W(a, b) = sum_{k >= max(a, b)} Y(k, a) Y(k, b), a <= b
     const int ntri = R * (R + 1) / 2;
