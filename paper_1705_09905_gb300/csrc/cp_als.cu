@@ -443,16 +443,28 @@ __global__ void k_apply(const float *M, const float *Wf, int64_t I, int R, float
     const int c = threadIdx.x % R, r0 = threadIdx.x / R, step = blockDim.x / R;
     __shared__ double red[1024];
     Dot2 sq;  // compensated FP32: a long FP64 chain is slow at GB300's FP64 rate
-    for (int r = r0; r < rows; r += step) {
-        Dot2 d;
+    // four rows at a time: four independent compensated chains in flight
+    for (int r = r0; r < rows; r += 4 * step) {
+        Dot2 d[4];
+        int rr[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rr[u] = min(r + u * step, rows - 1);
         for (int k = 0; k < R; ++k) {
-            const float m = sM[r * R + k];
-            d.add(m, sWh[k * R + c]);
-            d.add_small(m, sWl[k * R + c]);
+            const float wh = sWh[k * R + c], wl = sWl[k * R + c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float m = sM[rr[u] * R + k];
+                d[u].add(m, wh);
+                d[u].add_small(m, wl);
+            }
         }
-        const float s = __fadd_rn(d.s, d.c);
-        Fu[(i0 + r) * R + c] = s;
-        sq.add(s, s);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (r + u * step >= rows) break;
+            const float s = __fadd_rn(d[u].s, d[u].c);
+            Fu[(i0 + r + u * step) * R + c] = s;
+            sq.add(s, s);
+        }
     }
     red[r0 * R + c] = (double)sq.s + (double)sq.c;
     __syncthreads();
