@@ -368,38 +368,36 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_smem(GramList gl, int R
         // row k - 1 is final: scale it by 1 / l_(k-1)(k-1)
         if (k > 0)
             for (int c = tid; c < k; c += nt) Y[(k - 1) * R + c] *= s_inv[k - 1];
-        // rows i > k, columns c <= k: Y(i, c) -= l_ik * Y(k, c) / l_kk
-        const int w = k + 1, m = R - k - 1;
+        // rows i > k (a warp per row), columns c <= k (lanes along the row):
+        // Y(i, c) -= l_ik * Y(k, c) / l_kk
         const double rk = s_inv[k];
-        for (int e = tid; e < m * w; e += nt) {
-            const int i = k + 1 + e / w, c = e % w;
-            Y[i * R + c] = fma(-A[i * R + k] * rk, Y[k * R + c], Y[i * R + c]);
+        for (int i = k + 1 + warp; i < R; i += nwarps) {
+            const double t = A[i * R + k] * rk;
+            for (int c = lane; c <= k; c += 32) Y[i * R + c] = fma(-t, Y[k * R + c], Y[i * R + c]);
         }
         __syncthreads();
     }
     for (int c = tid; c < R; c += nt) Y[(R - 1) * R + c] *= s_inv[R - 1];
     __syncthreads();
-    // W(a, b) = sum_{k >= max(a, b)} Y(k, a) Y(k, b), a <= b
-    const int ntri = R * (R + 1) / 2;
-    for (int t = tid; t < ntri; t += nt) {
-        int a = 0, rem = t;  // row a of the upper triangle holds R - a entries
-        while (rem >= R - a) {
-            rem -= R - a;
-            ++a;
+    // W(a, b) = sum_{k >= max(a, b)} Y(k, a) Y(k, b) for a <= b: a warp per
+    // row a, lanes along b, four partial sums per entry
+    for (int a = warp; a < R; a += nwarps) {
+        for (int b = a + lane; b < R; b += 32) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int k = b;
+            for (; k + 3 < R; k += 4) {
+                s0 = fma(Y[k * R + a], Y[k * R + b], s0);
+                s1 = fma(Y[(k + 1) * R + a], Y[(k + 1) * R + b], s1);
+                s2 = fma(Y[(k + 2) * R + a], Y[(k + 2) * R + b], s2);
+                s3 = fma(Y[(k + 3) * R + a], Y[(k + 3) * R + b], s3);
+            }
+            for (; k < R; ++k) s0 = fma(Y[k * R + a], Y[k * R + b], s0);
+            const double w = (s0 + s1) + (s2 + s3);
+            W[a * R + b] = w;
+            W[b * R + a] = w;
+            split_store(Wf, R * R, a * R + b, w);
+            split_store(Wf, R * R, b * R + a, w);
         }
-        const int b = a + rem;
-        double s0 = 0.0, s1 = 0.0;
-        int k = b;
-        for (; k + 1 < R; k += 2) {
-            s0 = fma(Y[k * R + a], Y[k * R + b], s0);
-            s1 = fma(Y[(k + 1) * R + a], Y[(k + 1) * R + b], s1);
-        }
-        if (k < R) s0 = fma(Y[k * R + a], Y[k * R + b], s0);
-        const double w = s0 + s1;
-        W[a * R + b] = w;
-        W[b * R + a] = w;
-        split_store(Wf, R * R, a * R + b, w);
-        split_store(Wf, R * R, b * R + a, w);
     }
 }
 
