@@ -732,30 +732,29 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                     }
                     accumulate(b.vv[q], b.cr[q], slot, base, qt * Q + q);
                 }
-            } else if (NP == 1 && KIND == 0 && !p.segrow && has_out) {
+            } else if (NP == 1 && KIND == 0 && !p.segrow && has_out && !first && !in_smem) {
                 // SpTTM: fibres of one or two nonzeros are the norm, so segment
                 // starts take predicated stores and selects instead of a branch
                 // per nonzero (a warp's groups would diverge on almost every
-                // nonzero); only a run's first segment and segments that reached
-                // a fold take the general path
+                // nonzero).  Within a quarter nothing sets `first` or `in_smem`
+                // (folds happen at stage ends), so the test is made once per
+                // quarter; a run's first segment and segments that reached a
+                // fold take the general path.
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const bool hd = (hdm >> q) & 1u;
-                    if (hd && (first || in_smem)) {
-                        new_segment();
-                    } else {
 #pragma unroll
-                        for (int c = 0; c < NCH; ++c) {
-                            if (hd && act[c]) store_row<E>(orow + col[c], acc_st[c]);
+                    for (int c = 0; c < NCH; ++c) {
+                        if (hd && act[c]) store_row<E>(orow + col[c], acc_st[c]);
 #pragma unroll
-                            for (int e = 0; e < E; ++e) acc_st[c][e] = hd ? 0.f : acc_st[c][e];
-                        }
-                        seg += hd;
-                        row += hd;
-                        orow += hd ? R : 0;
+                        for (int e = 0; e < E; ++e) acc_st[c][e] = hd ? 0.f : acc_st[c][e];
                     }
+                    orow += hd ? R : 0;
                     accumulate(b.vv[q], b.cr[q], slot, base, qt * Q + q);
                 }
+                const int nh = __popc(hdm);
+                seg += nh;
+                row += nh;
             } else {
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
