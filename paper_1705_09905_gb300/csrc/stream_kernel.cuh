@@ -1,10 +1,10 @@
-// stream_kernel.cuh -- the F-COO streaming kernel (templates) shared by the
+// stream_kernel.cuh -- the F-COO streaming kernel (templates), shared by the
 // translation units that instantiate it for one factor type and one weight
 // kind each, so that nvcc compiles the variants in parallel.
-// The F-COO streaming kernel behind SpMTTKRP (Eq. 6) and
-// SpTTM (Eq. 3): one-shot product (Sec. IV-C) fused with the segmented
-// reduction over the bit-flags (Sec. IV-D).  The same kernel, with residual
-// weights, computes the sparse CP-fit loss and its adjoint.
+// It is the kernel behind SpMTTKRP (Eq. 6) and SpTTM (Eq. 3): the one-shot
+// product (Sec. IV-C) fused with the segmented reduction over the bit-flags
+// (Sec. IV-D).  The same kernel, with residual weights, computes the sparse
+// CP-fit loss and its adjoint.
 //
 // Work split (GB300 design; the paper's Maxwell layout of one thread per
 // column r and per threadlen partition is replaced):
@@ -13,34 +13,38 @@
 //     lane group; a run is a whole number of threadlen partitions, so the
 //     partition's start-flag tells whether the run opens a new segment;
 //   * a lane group of LPR lanes spans the R columns of one output row: each
-//     lane loads E contiguous elements (16 bytes) of every gathered factor row,
-//     so one row gather is a fully coalesced 64..512-byte access;
+//     lane holds E contiguous columns of every gathered factor row (eight:
+//     one 32-byte FP32 or 16-byte BF16 load; four for FP32 R <= 16; one on
+//     the scalar fallback), so one row gather is a fully coalesced access;
 //   * the group walks its run in stages of 32 nonzeros.  The index / value
 //     streams and the bit-flag word of a stage are copied by cp.async into a
-//     3-deep ring in shared memory, two stages ahead of use; groups' rings are
-//     offset by 16 bytes modulo 128 so that the 128-bit reads of one warp hit
-//     distinct banks;
-//   * gathers are software-pipelined in quarters of a stage (4 nonzeros, fully
-//     unrolled): the last-product-mode rows of quarter h+1 (and, for 3-way
-//     SpMTTKRP, the rows of the other product mode where a new fibre starts)
-//     are requested before quarter h is consumed, across stage boundaries
-//     too; a row address is one 32x32->64-bit multiply-add;
+//     two-slot ring in shared memory, one stage ahead of use; groups' rings
+//     are offset by 16 bytes modulo 128 so that the 128-bit reads of one warp
+//     hit distinct banks;
+//   * gathers are software-pipelined in "quarters" of Q nonzeros (2, or 4
+//     for four-column lanes), double-buffered in registers and walked by a
+//     rolled loop over quarter pairs: the last-product-mode rows of quarter
+//     h+1 (and, for 3-way SpMTTKRP, the rows of the other product mode where
+//     a new fibre starts) are requested before quarter h is consumed, across
+//     stage boundaries too; a row address is one 32x32->64-bit multiply-add;
 //   * the rows of the non-last product modes change only where a new fibre
 //     starts (fixed index mode and non-last product modes): their product brow
 //     is kept in registers and replaced by a predicated select, and each
 //     nonzero adds (val * brow) * row with the paired FP32 instructions
 //     (FMUL2 / FFMA2, two elements per instruction); only quarters that
-//     contain a segment start take a branch;
+//     contain a segment start take a branch (SpTTM, whose fibres are mostly
+//     one or two nonzeros long, takes predicated stores instead);
 //   * every 32 nonzeros the stage sum is folded into the segment sum with
-//     Kahan compensation, so the error of a long (Zipf-hot) segment grows with
-//     its number of stages, not nonzeros;
+//     Kahan compensation in shared memory, so the error of a long (Zipf-hot)
+//     segment grows with its number of stages, not nonzeros; a segment that
+//     starts and ends between two folds never leaves registers;
 //   * a segment that starts and ends inside a run is stored directly (one
-//     plain store per output row); segments cut by run boundaries are combined
-//     per CTA in shared memory (FP64, run order); segments cut by CTA
-//     boundaries leave one FP64 carry per CTA side, and k_carry_fixup adds the
-//     carries of each such segment in CTA order and stores the row.  No
-//     atomics on the output, no pre-zeroing, and the result is bitwise
-//     reproducible for a given handle, R and GPU.
+//     FP32 row per segment); segments cut by run boundaries are combined per
+//     CTA in shared memory (FP64, run order); segments cut by CTA boundaries
+//     leave one FP64 carry per CTA side, and k_carry_fixup adds the carries
+//     of each such segment in CTA order and stores the row.  No atomics on
+//     the output, no pre-zeroing, and the result is bitwise reproducible for
+//     a given handle, R and GPU.
 // The paper replaces atomics with a segmented scan whose inter-block carry is
 // passed by adjacent synchronisation (CTAs spinning on their predecessor); the
 // carry-slot + fixup pass gives the same atomic-free result without any CTA
