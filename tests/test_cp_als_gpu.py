@@ -110,6 +110,28 @@ def test_mixed_schedule_switches_storage(fc, oracle):
     assert np.isfinite(st.stats()["fit"])
 
 
+@pytest.mark.parametrize("R", [112, 120])
+def test_wide_rank_solves(fc, oracle, R):
+    """R = 112 is the largest rank whose solve runs in shared memory; R = 120
+    takes the global-memory solve.  Both match the oracle's mode updates."""
+    cfg = synth.scaled(synth.CONFIGS["tiny"], 30_000, dims=(400, 300, 250))
+    T = synth.make_tensor(cfg)
+    Xs = handles(fc, T)
+    init = synth.make_factors(T.dims, R, seed=6)
+    st = fc.CPState(T.dims, R, init)
+    st.iterate(Xs)
+    s = st.stats()
+    idx, val = T.idx_u32(), T.val.double().numpy()
+    F = [f.double().numpy() for f in init]
+    for n in range(3):
+        F, lam, _, used = oracle.cp_als_mode(T.dims, idx, val, F, n)
+        assert not used
+    assert s["npinv"] == 0
+    for k in range(3):
+        assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 1e-4, k
+    assert abs(s["fit"] - oracle.cp_fit(T.dims, idx, val, F, lam)) <= 1e-5
+
+
 def test_pseudo_inverse_fallback(fc, oracle):
     # modes 1 and 2 of size 1: the mode-0 normal matrix G1 * G2 has rank 1 < R
     T = synth.random_small((50, 1, 1), 30, seed=5)
