@@ -49,7 +49,7 @@ def test_status_strings(fc):
     assert fc.lib.fcoo_version() >= 10000
 
 
-@pytest.mark.parametrize("case", ["nmodes", "dims0", "mode", "op", "threadlen", "nullidx", "nnz"])
+@pytest.mark.parametrize("case", ["nmodes", "dims0", "mode", "op", "threadlen", "nullidx", "nnz", "nnz_max", "dims9"])
 def test_build_rejects_bad_arguments_without_device_work(fc, case):
     lib = fc.lib
     dims = (ctypes.c_uint32 * 3)(4, 5, 6)
@@ -72,6 +72,10 @@ def test_build_rejects_bad_arguments_without_device_work(fc, case):
         idx[2] = None
     elif case == "nnz":
         args["nnz"] = -5
+    elif case == "nnz_max":  # one past FCOO_MAX_NNZ (the padded streams must stay below 2^31)
+        args["nnz"] = 2147479552 + 1
+    elif case == "dims9":  # more modes than FCOO_MAX_MODES
+        args["nmodes"] = 9
     out = ctypes.c_void_p(1234)
     st = lib.fcoo_build(args["nmodes"], args["dims"], args["nnz"], ctypes.cast(idx, ctypes.POINTER(ctypes.c_void_p)),
                         args["val"], args["mode"], args["op"], args["threadlen"], None, ctypes.byref(out))
