@@ -37,6 +37,10 @@ struct cp_state {
     int *flags;                     // [0] pseudo-inverse solves, [1] non-finite seen
     int iters;
     bool have_norm;
+    // the R x R solve of mode n runs on `side` while SpMTTKRP of mode n runs
+    // on the caller's stream (it needs only the other modes' Grams)
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
     void *base;
     size_t bytes;
 };
@@ -665,6 +669,23 @@ int gram_of(cp_state_t *st, int k, cudaStream_t s) {
 int mode_update(const fcoo_t *X, cp_state_t *st, int n, bool last, cudaStream_t s) {
     const int R = st->R;
     const int64_t I = st->dims[n];
+    // V = Hadamard of the other modes' Grams and V^-1: on the side stream,
+    // overlapped with SpMTTKRP (one CTA beside a grid that leaves it a slot)
+    GramList gl;
+    memset(&gl, 0, sizeof(gl));
+    for (int k = 0; k < st->nmodes; ++k)
+        if (k != n) gl.g[gl.n++] = st->gram[k];
+    FCOO_CUDA(cudaEventRecord(st->ev_fork, s));
+    FCOO_CUDA(cudaStreamWaitEvent(st->side, st->ev_fork, 0));
+    if (R <= kSolveSmemMaxR) {
+        const int smem = 2 * R * R * 8;
+        FCOO_CUDA(cudaFuncSetAttribute(k_solve_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_solve_smem<<<1, kSolveThreads, smem, st->side>>>(gl, R, st->V, st->Q, st->W, st->Wf, st->flags);
+    } else {
+        k_solve<<<1, kSolveThreads, 0, st->side>>>(gl, R, st->V, st->Q, st->W, st->Wf, st->flags);
+    }
+    FCOO_CUDA(cudaGetLastError());
+    FCOO_CUDA(cudaEventRecord(st->ev_join, st->side));
     // M = SpMTTKRP_n
     StreamParams p;
     stream_params_from(X, p);
@@ -672,25 +693,14 @@ int mode_update(const fcoo_t *X, cp_state_t *st, int n, bool last, cudaStream_t 
     p.out = st->M;
     p.R = R;
     p.out_rows = I;
+    p.reserve_ctas = 1;
     if (X->nnz == 0) {
         FCOO_CUDA(cudaMemsetAsync(st->M, 0, (size_t)I * R * 4, s));
     } else {
         int rc = launch_stream_kernel(p, st->dtype, s);
         if (rc) return rc;
     }
-    // V, V^-1
-    GramList gl;
-    memset(&gl, 0, sizeof(gl));
-    for (int k = 0; k < st->nmodes; ++k)
-        if (k != n) gl.g[gl.n++] = st->gram[k];
-    if (R <= kSolveSmemMaxR) {
-        const int smem = 2 * R * R * 8;
-        FCOO_CUDA(cudaFuncSetAttribute(k_solve_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_solve_smem<<<1, kSolveThreads, smem, s>>>(gl, R, st->V, st->Q, st->W, st->Wf, st->flags);
-    } else {
-        k_solve<<<1, kSolveThreads, 0, s>>>(gl, R, st->V, st->Q, st->W, st->Wf, st->flags);
-    }
-    FCOO_CUDA(cudaGetLastError());
+    FCOO_CUDA(cudaStreamWaitEvent(s, st->ev_join, 0));
     // Fu = M W, column norms
     const int nb = (int)ceil_div(I, kRowsPerBlock);
     const int threads = R >= 256 ? R : (256 / R) * R;  // a multiple of R
@@ -794,6 +804,9 @@ extern "C" int cp_state_create(int nmodes, const uint32_t *dims, int R, int dtyp
         }
         if (rc == FCOO_OK) rc = gram_of(st, k, s);
     }
+    if (rc == FCOO_OK) cu(cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (rc == FCOO_OK) cu(cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    if (rc == FCOO_OK) cu(cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     {
         double ones[FCOO_MAX_RANK];
         for (int r = 0; r < R; ++r) ones[r] = 1.0;
@@ -801,6 +814,9 @@ extern "C" int cp_state_create(int nmodes, const uint32_t *dims, int R, int dtyp
         cu(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     }
     if (rc != FCOO_OK) {
+        if (st->ev_join) cudaEventDestroy(st->ev_join);
+        if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+        if (st->side) cudaStreamDestroy(st->side);
         dev_free(st->base);
         free(st);
         return rc;
@@ -842,6 +858,9 @@ extern "C" int cp_state_destroy(cp_state_t *st) {
     clear_error();
     if (!st) return FCOO_OK;
     cudaDeviceSynchronize();
+    if (st->ev_join) cudaEventDestroy(st->ev_join);
+    if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+    if (st->side) cudaStreamDestroy(st->side);
     dev_free(st->base);
     free(st);
     return FCOO_OK;

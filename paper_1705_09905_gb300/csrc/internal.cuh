@@ -112,6 +112,7 @@ struct StreamParams {
     int nprod;
     int threadlen;
     int grid;
+    int reserve_ctas;   // CTA slots left free for a kernel running beside this one
     int64_t cta_chunk;  // nonzeros per CTA (multiple of groups * run alignment)
     int64_t run_len;    // nonzeros per group run
 };

@@ -994,7 +994,8 @@ int launch_variant(StreamParams &p, cudaStream_t s) {
         cached_smem = smem;
     }
     const int64_t ra = p.threadlen > 32 ? p.threadlen : 32;
-    const int64_t max_ctas = std::min<int64_t>((int64_t)sms() * cached_occ, p.grid);
+    const int64_t max_ctas =
+        std::max<int64_t>(1, std::min<int64_t>((int64_t)sms() * cached_occ - p.reserve_ctas, p.grid));
     int64_t grid = std::min<int64_t>(max_ctas, ceil_div(p.nnz, (int64_t)G * ra));
     if (grid < 1) grid = 1;
     p.run_len = round_up(ceil_div(p.nnz, grid * G), ra);
