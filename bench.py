@@ -303,6 +303,56 @@ def bench_spttm(fc, dev, quick, nnz=0):
             "alg_bytes": byt, "GBps": byt / t / 1e9, "GFLOPs": 2 * 16 * X.nnz / t / 1e9}
 
 
+def _time_calls(fn, n=20, warm=3):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(n):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / n
+
+
+def bench_sweep(fc, dev, quick):
+    """Mode and rank sweep: SpTTM along every mode of the 4-way workload
+    (R = 16) and SpMTTKRP of every mode of the skewed 3-way workload at
+    R = 8, 16, 32, 64 (FP32 factors).  GB/s of algorithmic bytes per call."""
+    out = {"spttm_modes": [], "spmttkrp_ranks": []}
+    cfg = synth.CONFIGS["ttm4"]
+    if quick:
+        cfg = synth.scaled(cfg, 4_000_000, dims=(500, 400, 300, 50_000))
+    T = synth.make_tensor(cfg, device=dev)
+    idx32 = [a.to(torch.int32).contiguous() for a in T.idx]
+    for n in range(len(cfg.dims)):
+        X = fc.FCOO.build(idx32, T.val, cfg.dims, n, "ttm", 8)
+        U = synth.make_factors([cfg.dims[n]], 16, seed=1, device=dev)[0]
+        Y = torch.empty((X.nseg, 16), device=dev)
+        t = _time_calls(lambda: fc.spttm(X, U, out=Y))
+        byt = ttm_alg_bytes(X, 16, 4)
+        out["spttm_modes"].append({"mode": n, "dim": cfg.dims[n], "nfib": X.nseg, "ms": t * 1e3,
+                                   "GBps": byt / t / 1e9, "pct_hbm": byt / t / 1e9 / peaks()[0]})
+        del Y, X
+        torch.cuda.empty_cache()
+    del T, idx32
+    cfg = synth.CONFIGS["skewed3"] if not quick else synth.scaled(synth.CONFIGS["skewed3"], 4_000_000,
+                                                                 dims=(1200, 900, 2800))
+    _, Xs, _, _ = build_workload(cfg, dev)
+    for R in (8, 16, 32, 64):
+        F = [f.to(dev) for f in synth.make_factors(cfg.dims, R, seed=1)]
+        row = {"R": R, "modes": []}
+        for n in range(3):
+            M = torch.empty((cfg.dims[n], R), device=dev)
+            t = _time_calls(lambda: fc.spmttkrp(Xs[n], F, out=M))
+            byt = mttkrp_alg_bytes(Xs[n], R, 4)
+            row["modes"].append({"mode": n, "ms": t * 1e3, "GBps": byt / t / 1e9,
+                                 "pct_hbm": byt / t / 1e9 / peaks()[0]})
+        out["spmttkrp_ranks"].append(row)
+    return out
+
+
 def bench_mttkrp_bf16(fc, Xs, dims, R, steps=50):
     """The same three SpMTTKRP calls with BF16 factors (FP32 accumulation):
     half the gathered bytes per nonzero."""
@@ -528,9 +578,10 @@ def main():
     ap.add_argument("--rank", type=int, default=0, help="override R")
     ap.add_argument("--cpu-sample", type=int, default=40_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
-    ap.add_argument("--part", default="all", choices=["all", "spttm", "cp", "fit"],
+    ap.add_argument("--part", default="all", choices=["all", "spttm", "cp", "fit", "sweep"],
                     help="only one extra line, for profiling: spttm (4-way workload, --nnz scales it), "
-                         "cp (CP-ALS on the skewed 3-way workload) or fit (sparse CP fit)")
+                         "cp (CP-ALS on the skewed 3-way workload), fit (sparse CP fit) or sweep "
+                         "(SpTTM along every mode, SpMTTKRP at R = 8..64)")
     ap.add_argument("--sweeps", type=int, default=20, help="CP-ALS sweeps of the cp line")
     args = ap.parse_args()
     if args.part != "all":
@@ -541,6 +592,8 @@ def main():
             line = bench_spttm(fc, dev, args.quick, args.nnz)
         elif args.part == "fit":
             line = bench_sparse_fit(fc, dev, args.quick)
+        elif args.part == "sweep":
+            line = bench_sweep(fc, dev, args.quick)
         else:
             cfg = workload_config(args)
             _, Xs, _, _ = build_workload(cfg, dev)
