@@ -12,6 +12,7 @@ for the passage of the paper each routine follows:
 
 * ``mttkrp``        -- Eq. 5 / Eq. 6, Table I row 2 (SpMTTKRP on mode n)
 * ``ttm``           -- Eq. 3, Table I row 1 (SpTTM, semi-sparse output)
+* ``ttmc``          -- Eq. 4, Table I row 3 (SpTTMc, dense Kronecker-row output)
 * ``fcoo_layout``   -- Sec. IV-B, Table I, Fig. 2 caption (sort order, flags)
 * ``cp_als``        -- Algorithm 1 (CP-ALS), N-way
 * ``spd_solve``     -- the ``V^dagger`` of Algorithm 1 (Cholesky / pinv)
@@ -59,6 +60,7 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.orc_mttkrp.restype = ctypes.c_int
             lib.orc_ttm.restype = ctypes.c_int64
+            lib.orc_ttmc.restype = ctypes.c_int
             lib.orc_fcoo_layout.restype = ctypes.c_int
             lib.orc_cp_als.restype = ctypes.c_int
             lib.orc_spd_solve.restype = ctypes.c_int
@@ -110,6 +112,21 @@ def mttkrp(dims, idx, val, factors, mode):
     out = np.empty((int(c.dims[mode]), R), dtype=np.float64)
     _check(lib.orc_mttkrp(c.nmodes, c.dims_ptr, ctypes.c_int64(c.nnz), c.idx_ptrs, val.ctypes.data_as(_f64p),
                           _ptr_table(fs), R, mode, out.ctypes.data_as(_f64p)))
+    return out
+
+
+def ttmc(dims, idx, val, factors, mode):
+    """SpTTMc on ``mode`` (Eq. 4): returns dims[mode] x R^(N-1) float64, the
+    output column of (r_a, r_b, ...) over the product modes in ascending order
+    being ((r_a * R) + r_b) * R + ... (first product mode slowest)."""
+    lib = _load()
+    c = _Coo(dims, idx)
+    val = _f64(val)
+    R = int(np.asarray(factors[(mode + 1) % c.nmodes]).shape[1])
+    fs = [(_f64(f) if k != mode else np.zeros((1, R))) for k, f in enumerate(factors)]
+    out = np.empty((int(c.dims[mode]), R ** (c.nmodes - 1)), dtype=np.float64)
+    _check(lib.orc_ttmc(c.nmodes, c.dims_ptr, ctypes.c_int64(c.nnz), c.idx_ptrs, val.ctypes.data_as(_f64p),
+                        _ptr_table(fs), R, mode, out.ctypes.data_as(_f64p)))
     return out
 
 

@@ -66,6 +66,43 @@ int orc_mttkrp(int nmodes, const uint32_t *dims, int64_t nnz, const uint32_t *co
 }
 
 /* ------------------------------------------------------------------------ */
+/* SpTTMc along `mode` (Eq. 4, Table I row 3): the tensor times a matrix on  */
+/* every other mode, written per nonzero as the row-vector Kronecker product */
+/*   Y_(mode)(i_mode, :) += val * (U_a(i_a, :) (x) U_b(i_b, :) (x) ...)      */
+/* over the product modes a < b < ... in ascending mode order, all of rank R. */
+/* Output column c = (((r_a * R) + r_b) * R + ...) (the first product mode    */
+/* varies slowest); out is dims[mode] x R^(nmodes-1), row-major.             */
+/* ------------------------------------------------------------------------ */
+int orc_ttmc(int nmodes, const uint32_t *dims, int64_t nnz, const uint32_t *const *idx,
+             const double *val, const double *const *factors, int R, int mode, double *out)
+{
+    int st = check_coo(nmodes, dims, nnz, idx);
+    if (st) return st;
+    if (mode < 0 || mode >= nmodes || R <= 0 || !out || nmodes < 2) return ORC_ERR_ARG;
+    int64_t width = 1;
+    for (int k = 0; k < nmodes - 1; ++k) width *= R;
+    memset(out, 0, sizeof(double) * (size_t)dims[mode] * (size_t)width);
+    int rr[ORC_MAX_MODES];
+    for (int64_t p = 0; p < nnz; ++p) {
+        double *row = out + (size_t)idx[mode][p] * (size_t)width;
+        for (int64_t c = 0; c < width; ++c) {
+            /* digits of c in base R, most significant first = first product mode */
+            int64_t q = c;
+            for (int t = nmodes - 2; t >= 0; --t) {
+                rr[t] = (int)(q % R);
+                q /= R;
+            }
+            double v = val[p];
+            int t = 0;
+            for (int k = 0; k < nmodes; ++k)
+                if (k != mode) v *= factors[k][(size_t)idx[k][p] * R + rr[t++]];
+            row[c] += v;
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Lexicographic comparison of two nonzeros over a list of modes.            */
 /* The sort below is a library primitive used only to enumerate the          */
 /* distinct index tuples of the semi-sparse output (Sec. II, Eq. 3) and the  */

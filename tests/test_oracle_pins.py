@@ -7,6 +7,8 @@ fit formula) fails at least one of them:
 * brute force on tiny tensors: densify, unfold X_(n) (Sec. II), build the
   Khatri-Rao product explicitly column by column from Kronecker products
   (Eq. 1, Eq. 2) and multiply (Eq. 5); SpTTM via a dense n-mode product (Eq. 3);
+  SpTTMc via chained dense n-mode products and via X_(n) times a Kronecker
+  product (Eq. 4);
 * closed forms for a full Kruskal tensor;
 * hand-derived golden values (tests/golden, Fig. 2 / Table I / Eq. 3 / Eq. 6);
 * special cases (R=1 all-ones factors give slice sums, identity U);
@@ -211,6 +213,87 @@ def test_ttm_golden_fig2(oracle):
     keys, Y = oracle.ttm(g["dims"], idx, val, np.array(t["U"]), 2)
     np.testing.assert_array_equal(keys, np.array(t["segkeys"]))
     np.testing.assert_array_equal(Y, np.array(t["Y"]))
+
+
+# ---------------------------------------------------------------- SpTTMc
+
+
+def dense_ttmc(X, U, n):
+    """Eq. 4 on a dense tensor: X times U_k^T on every mode k != n, the product
+    modes kept in ascending order; reshaped so the first product mode varies
+    slowest in the output column."""
+    Y = X
+    for k in sorted((k for k in range(X.ndim) if k != n), reverse=True):
+        Y = np.moveaxis(np.tensordot(Y, U[k], axes=([k], [0])), -1, k)
+    Y = np.moveaxis(Y, n, 0)
+    return Y.reshape(X.shape[n], -1)
+
+
+@pytest.mark.parametrize("dims,mode", [((6, 5, 4), 0), ((6, 5, 4), 1), ((6, 5, 4), 2), ((4, 3, 5, 3), 0),
+                                       ((4, 3, 5, 3), 2)])
+def test_ttmc_matches_dense_products(oracle, dims, mode):
+    rng = np.random.default_rng(21)
+    nnz = int(np.prod(dims) * 0.35)
+    idx, val = rand_coo(rng, dims, nnz)
+    R = 3
+    U = [rng.standard_normal((d, R)) for d in dims]
+    U[mode] = np.full((dims[mode], R), np.nan)  # the index mode's factor is never read
+    got = oracle.ttmc(dims, idx, val, U, mode)
+    X = densify(dims, idx, val)
+    np.testing.assert_allclose(got, dense_ttmc(X, U, mode), rtol=1e-12, atol=1e-12)
+    # the same through the unfolding: X_(n) times the Kronecker product of the
+    # product-mode factors (Eq. 1), lowest mode fastest in both; then the
+    # column digits reversed so the first product mode is the slowest
+    others = [k for k in range(len(dims)) if k != mode]
+    K = U[others[-1]]
+    for k in reversed(others[:-1]):
+        K = np.kron(K, U[k])
+    Yu = (unfold(X, mode) @ K).reshape([dims[mode]] + [R] * len(others))
+    Yu = np.transpose(Yu, [0] + list(range(len(others), 0, -1))).reshape(dims[mode], -1)
+    np.testing.assert_allclose(got, Yu, rtol=1e-12, atol=1e-12)
+
+
+def test_ttmc_identity_densifies_and_kruskal_closed_form(oracle):
+    rng = np.random.default_rng(22)
+    dims = (4, 5, 5)
+    idx, val = rand_coo(rng, dims, 50)
+    U = [np.zeros((4, 5)), np.eye(5), np.eye(5)]
+    got = oracle.ttmc(dims, idx, val, U, 0)
+    np.testing.assert_array_equal(got, densify(dims, idx, val).reshape(4, 25))
+    # full Kruskal tensor: Y(i, p, q) = sum_r lam_r A(i,r) (U1^T B)(p,r) (U2^T C)(q,r)
+    dims = (6, 5, 4)
+    A, B, C = (rng.standard_normal((d, 2)) for d in dims)
+    lam = np.array([1.3, -0.6])
+    Xk = np.einsum("r,ir,jr,kr->ijk", lam, A, B, C)
+    fidx = [a.astype(np.uint32).ravel() for a in np.indices(dims)]
+    U1, U2 = rng.standard_normal((5, 3)), rng.standard_normal((4, 3))
+    got = oracle.ttmc(dims, fidx, Xk.ravel(), [np.zeros((6, 3)), U1, U2], 0)
+    ref = np.einsum("r,ir,pr,qr->ipq", lam, A, U1.T @ B, U2.T @ C).reshape(6, 9)
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("dims,mode", [((6, 5, 4), 1), ((4, 3, 5, 3), 3)])
+def test_ttmc_diagonal_is_mttkrp(oracle, dims, mode):
+    rng = np.random.default_rng(23)
+    idx, val = rand_coo(rng, dims, int(np.prod(dims) * 0.4))
+    R = 3
+    U = [rng.standard_normal((d, R)) for d in dims]
+    Y = oracle.ttmc(dims, idx, val, U, mode)
+    nprod = len(dims) - 1
+    diag = [sum(r * R ** e for e in range(nprod)) for r in range(R)]
+    np.testing.assert_allclose(Y[:, diag], oracle.mttkrp(dims, idx, val, U, mode), rtol=1e-12, atol=1e-12)
+
+
+def test_ttmc_single_nonzero_and_empty(oracle):
+    dims = (3, 4, 2)
+    idx = [np.array([2], np.uint32), np.array([1], np.uint32), np.array([0], np.uint32)]
+    U = [np.zeros((3, 2)), np.array([[0, 0], [2.0, 3.0], [0, 0], [0, 0]]), np.array([[5.0, 7.0], [0, 0]])]
+    Y = oracle.ttmc(dims, idx, np.array([0.5]), U, 0)
+    ref = np.zeros((3, 4))
+    ref[2] = 0.5 * np.array([2 * 5, 2 * 7, 3 * 5, 3 * 7])
+    np.testing.assert_array_equal(Y, ref)
+    empty = [np.zeros(0, np.uint32)] * 3
+    np.testing.assert_array_equal(oracle.ttmc(dims, empty, np.zeros(0), U, 0), np.zeros((3, 4)))
 
 
 # ---------------------------------------------------------------- F-COO layout
