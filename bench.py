@@ -303,6 +303,44 @@ def bench_spttm(fc, dev, quick, nnz=0):
             "alg_bytes": byt, "GBps": byt / t / 1e9, "GFLOPs": 2 * 16 * X.nnz / t / 1e9}
 
 
+def ttmc_alg_bytes(X, R: int) -> int:
+    """Compulsory bytes of one SpTTMc call: the Table II stream, the segment
+    map, the product-mode factor rows read once, the R^(N-1)-wide output
+    written once (FP32)."""
+    b = X.bytes["table2"] + X.bytes["segmap"]
+    b += sum(X.dims[k] * R * 4 for k in X.prod_modes)
+    b += X.dims[X.mode] * R ** (X.nmodes - 1) * 4
+    return int(b)
+
+
+def fp32_alu_peak_tflops(dev, sm_mhz: float = 2070.0) -> float:
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x the maximum SM clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def bench_spttmc(fc, Xs, dims, dev):
+    """SpTTMc (Eq. 4) of every mode of the skewed 3-way workload at R = 8 and
+    16 (output widths 64 and 256), FP32 factors, on the SpMTTKRP handles.
+    Each nonzero costs R^2 FMAs: the kernel is bound by FP32 issue, not
+    HBM, so the roofline is the FP32 FMA peak."""
+    peak = fp32_alu_peak_tflops(dev)
+    res = {"alu_peak_tflops": peak, "peak_source": "SMs x 128 FP32 lanes x 2 x 2070 MHz", "ranks": []}
+    for R in (16, 8):
+        F = [f.to(dev) for f in synth.make_factors(dims, R, seed=1)]
+        row = {"R": R, "width": R * R, "modes": []}
+        for n in range(3):
+            Y = torch.empty((dims[n], R * R), device=dev)
+            t = _time_calls(lambda: fc.spttmc(Xs[n], F, out=Y))
+            fl = 2 * R * R * Xs[n].nnz
+            byt = ttmc_alg_bytes(Xs[n], R)
+            row["modes"].append({"mode": n, "ms": t * 1e3, "TFLOPs": fl / t / 1e12, "frac_alu": fl / t / 1e12 / peak,
+                                 "GBps": byt / t / 1e9, "pct_hbm": byt / t / 1e9 / peaks()[0]})
+            del Y
+        res["ranks"].append(row)
+    return res
+
+
 def _time_calls(fn, n=20, warm=3):
     for _ in range(warm):
         fn()
@@ -518,6 +556,7 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         for name, fn in (("mttkrp_bf16", lambda: bench_mttkrp_bf16(fc, Xs, cfg.dims, R)),
                          ("spttm", lambda: bench_spttm(fc, dev, args.quick)),
+                         ("spttmc", lambda: bench_spttmc(fc, Xs, cfg.dims, dev)),
                          ("cp_als", lambda: bench_cp_als(fc, Xs, cfg.dims, 20 if not args.quick else 5)),
                          ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick))):
             try:
@@ -578,8 +617,9 @@ def main():
     ap.add_argument("--rank", type=int, default=0, help="override R")
     ap.add_argument("--cpu-sample", type=int, default=40_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
-    ap.add_argument("--part", default="all", choices=["all", "spttm", "cp", "fit", "sweep"],
+    ap.add_argument("--part", default="all", choices=["all", "spttm", "spttmc", "cp", "fit", "sweep"],
                     help="only one extra line, for profiling: spttm (4-way workload, --nnz scales it), "
+                         "spttmc (SpTTMc of every mode of the skewed 3-way workload, R = 8 and 16), "
                          "cp (CP-ALS on the skewed 3-way workload), fit (sparse CP fit) or sweep "
                          "(SpTTM along every mode, SpMTTKRP at R = 8..64)")
     ap.add_argument("--sweeps", type=int, default=20, help="CP-ALS sweeps of the cp line")
@@ -594,6 +634,10 @@ def main():
             line = bench_sparse_fit(fc, dev, args.quick)
         elif args.part == "sweep":
             line = bench_sweep(fc, dev, args.quick)
+        elif args.part == "spttmc":
+            cfg = workload_config(args)
+            _, Xs, _, _ = build_workload(cfg, dev)
+            line = bench_spttmc(fc, Xs, cfg.dims, dev)
         else:
             cfg = workload_config(args)
             _, Xs, _, _ = build_workload(cfg, dev)

@@ -201,6 +201,29 @@ int spmttkrp(const fcoo_t *X, const void *const *factors, int dtype, int R, floa
 int spttm(const fcoo_t *X, const void *U, int dtype, int R, float *out, fcoo_stream_t stream);
 
 /* ---------------------------------------------------------------------- */
+/* SpTTMc (Eq. 4, Table I row 3): the tensor times a matrix on every mode  */
+/* but one, the core of Tucker decomposition by HOOI (Sec. II)            */
+/* ---------------------------------------------------------------------- */
+
+/* out(i, c) = sum over nonzeros p with idx_mode(p) = i of
+ *             val(p) * prod_{t} U_{k_t}(idx_{k_t}(p), r_t)
+ * where k_0 < k_1 < ... are the modes other than `mode` and the output column
+ * c = ((r_0 * R + r_1) * R + ...) holds the digits r_t of the row-vector
+ * Kronecker product U_{k_0}(j, :) (x) U_{k_1}(k, :) (x) ... (Eq. 1); the
+ * first product mode varies slowest.
+ * X        handle built with op = FCOO_OP_MTTKRP (the same handle SpMTTKRP uses)
+ * factors  host array of N device pointers; factors[k] is dims[k] x R FP32
+ *          row-major; factors[mode] is not read (may be NULL)
+ * dtype    FCOO_F32 (FCOO_BF16 returns FCOO_ERR_UNSUPPORTED)
+ * R        per-mode rank, R >= 1 with R^(N-1) <= FCOO_MAX_RANK
+ *          (FCOO_ERR_UNSUPPORTED above)
+ * out      device float32 dims[mode] x R^(N-1), row-major; every element is
+ *          written (rows without nonzeros are set to 0)
+ * Deterministic for a given handle and R, like spmttkrp.  Asynchronous on
+ * `stream`. */
+int spttmc(const fcoo_t *X, const void *const *factors, int dtype, int R, float *out, fcoo_stream_t stream);
+
+/* ---------------------------------------------------------------------- */
 /* SpMTTKRP for callers that cannot allocate device memory                  */
 /* ---------------------------------------------------------------------- */
 

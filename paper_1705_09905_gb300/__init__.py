@@ -194,6 +194,35 @@ def spttm(X: FCOO, U: torch.Tensor, out: Optional[torch.Tensor] = None, stream=N
     return out
 
 
+def spttmc(X: FCOO, factors: Sequence[Optional[torch.Tensor]], out: Optional[torch.Tensor] = None,
+           stream=None) -> torch.Tensor:
+    """SpTTMc on the handle's mode (Eq. 4) with FP32 factors of one rank R:
+    dims[mode] x R^(N-1) float32, column ((r_a * R) + r_b) * R + ... over the
+    other modes a < b < ... (the first slowest).  Takes an SpMTTKRP handle."""
+    if X.op != MTTKRP:
+        raise ValueError("SpTTMc takes a handle built for SpMTTKRP")
+    ref = factors[X.prod_modes[0]]
+    R = int(ref.shape[1])
+    ptrs = []
+    for k in range(X.nmodes):
+        if k == X.mode:
+            ptrs.append(None)
+            continue
+        f = factors[k]
+        _check_factor(f, X.dims[k], R, f"factors[{k}]")
+        if f.dtype != torch.float32:
+            raise TypeError("SpTTMc takes float32 factors")
+        ptrs.append(f.data_ptr())
+    if out is None:
+        out = torch.empty((X.dims[X.mode], R ** (X.nmodes - 1)), dtype=torch.float32, device=ref.device)
+    pp, _keep = ptr_array(ptrs)
+    check(lib.spttmc(X.handle, pp, F32, R, out.data_ptr(), _stream(stream)))
+    return out
+
+
+__all__ += ["spttmc"]
+
+
 # ---------------------------------------------------------------- CP-ALS (Algorithm 1)
 
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "fcoo_fibre_indices": (_i, [_vp, _vp, _vp]),
     "spmttkrp": (_i, [_vp, _vpp, _i, _i, _vp, _vp]),
     "spttm": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "spttmc": (_i, [_vp, _vpp, _i, _i, _vp, _vp]),
     "spmttkrp_noalloc": (_i, [ctypes.POINTER(FcooView), _vpp, _i, _i, _vp, _vp]),
     "cp_state_create": (_i, [_i, _vp, _i, _i, _vpp, _vp, ctypes.POINTER(_vp)]),
     "cp_state_destroy": (_i, [_vp]),

@@ -108,7 +108,8 @@ struct StreamParams {
     int64_t nnz;
     int64_t nseg;
     int64_t out_rows;
-    int R;
+    int R;              // output row width (SpTTMc: Rin^nprod)
+    int Rin;            // SpTTMc: rank of every factor; unused by the other kinds
     int nprod;
     int threadlen;
     int grid;
@@ -121,12 +122,14 @@ struct StreamParams {
 void stream_params_from(const fcoo_t *X, StreamParams &p);
 
 // Launch the segmented-reduction kernel for dtype / R (spmttkrp.cu); kind 0
-// weights every nonzero by its value, kind 1 by the residual weight above.
+// weights every nonzero by its value, kind 1 by the residual weight above,
+// kind 2 by its value with Kronecker output columns (SpTTMc, FP32 factors).
 int launch_stream_kernel(StreamParams &p, int dtype, cudaStream_t s, int kind = 0);
 // The instantiations, one translation unit each (stream_*.cu).
 int launch_stream_f32_k0(StreamParams &p, cudaStream_t s);
 int launch_stream_f32_k1(StreamParams &p, cudaStream_t s);
 int launch_stream_bf16_k0(StreamParams &p, cudaStream_t s);
 int launch_stream_bf16_k1(StreamParams &p, cudaStream_t s);
+int launch_stream_f32_k2(StreamParams &p, cudaStream_t s);
 
 }  // namespace fcx

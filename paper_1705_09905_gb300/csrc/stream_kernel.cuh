@@ -4,7 +4,8 @@
 // It is the kernel behind SpMTTKRP (Eq. 6) and SpTTM (Eq. 3): the one-shot
 // product (Sec. IV-C) fused with the segmented reduction over the bit-flags
 // (Sec. IV-D).  The same kernel, with residual weights, computes the sparse
-// CP-fit loss and its adjoint.
+// CP-fit loss and its adjoint, and, with Kronecker output columns, SpTTMc
+// (Eq. 4, Table I row 3).
 //
 // Work split (GB300 design; the paper's Maxwell layout of one thread per
 // column r and per threadlen partition is replaced):
@@ -161,6 +162,14 @@ struct RowIO<__nv_bfloat16, 1> {
     static __device__ __forceinline__ void cvt(const raw &r, float (&v)[1]) { v[0] = __uint_as_float((uint32_t)r << 16); }
 };
 
+// one factor element as FP32
+template <typename TF>
+__device__ __forceinline__ float ld_elem(const TF *p) {
+    float v[1];
+    RowIO<TF, 1>::cvt(RowIO<TF, 1>::load(p), v);
+    return v[0];
+}
+
 template <int E>
 __device__ __forceinline__ void store_row(float *dst, const float (&v)[E]) {
     if constexpr (E == 4) {
@@ -296,7 +305,10 @@ __device__ __forceinline__ void zero_rows(float *out, int R, int lig, int64_t fr
 // vector variants); LPR: lanes per group; NCH: column chunks per lane
 // (columns of lane l, chunk c: (c * LPR + l) * E ... + E - 1); NP: number of
 // product modes (0: runtime value p.nprod); KIND: 0 = value weights
-// (SpMTTKRP / SpTTM), 1 = residual weights.
+// (SpMTTKRP / SpTTM), 1 = residual weights, 2 = value weights with Kronecker
+// output columns (SpTTMc: the R = Rin^nprod columns of a row are the base-Rin
+// digit tuples of the product modes, the first product mode most significant;
+// a lane's E columns share every digit but the last).
 // Resident CTAs per SM the register budget is set for: 3 (80 registers) for
 // the one-product value pass with at most four columns per lane (SpTTM at
 // R <= 16: short segments, two-nonzero quarters; measured 9 % faster with 24
@@ -361,6 +373,16 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
     int colc[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) colc[c] = act[c] ? col[c] : 0;
+    // factor row width: R, or the per-mode rank Rin of SpTTMc, whose last
+    // product mode is read at the last digit of the column and whose first
+    // (3-way) contributes the single element at the first digit
+    const int Rin = KIND == 2 ? p.Rin : R;
+    int colL[NCH], colB[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        colL[c] = KIND == 2 ? colc[c] % Rin : colc[c];
+        colB[c] = KIND == 2 ? colc[c] / Rin : colc[c];
+    }
     const TF *Fl = static_cast<const TF *>(p.F[nprod - 1]);
     const TF *Fb = static_cast<const TF *>(p.F[0]);
 
@@ -583,6 +605,26 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                         for (int e = 0; e < E; ++e) acc_st[c][e] = fmaf(v * brow[c][e], t[c][e], acc_st[c][e]);
                     }
                 }
+            } else if constexpr (KIND == 2) {
+                // Kronecker columns: brow is one element per chunk (the
+                // non-last product modes' entries at this lane's digits)
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const float sc = v * brow[c][0];
+                    if constexpr (E % 2 == 0) {
+                        const float2 s2 = make_float2(sc, sc);
+#pragma unroll
+                        for (int e = 0; e < E; e += 2) {
+                            const float2 a = __ffma2_rn(s2, make_float2(t[c][e], t[c][e + 1]),
+                                                        make_float2(acc_st[c][e], acc_st[c][e + 1]));
+                            acc_st[c][e] = a.x;
+                            acc_st[c][e + 1] = a.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) acc_st[c][e] = fmaf(sc, t[c][e], acc_st[c][e]);
+                    }
+                }
             } else {
                 // h = brow * row; e = <T(row), h> - val; acc_st += e * h
                 float h[NCH][E];
@@ -615,6 +657,22 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         };
         // brow from the rows of the non-last product modes (general N)
         auto set_brow_sync = [&](const unsigned char *slot, int u) {
+            if constexpr (KIND == 2) {
+                // the product of F_m(k_m, digit m of the column), m < nprod - 1
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    int q = colB[c];
+                    float b = 1.f;
+                    for (int m = nprod - 2; m >= 0; --m) {
+                        const TF *Fm = static_cast<const TF *>(p.F[m]);
+                        const uint32_t km = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[u];
+                        b *= ld_elem(Fm + (size_t)km * Rin + q % Rin);
+                        q /= Rin;
+                    }
+                    brow[c][0] = b;
+                }
+                return;
+            }
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
 #pragma unroll
@@ -636,13 +694,13 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         for (int m = 0; m < FCOO_MAX_MODES - 1; ++m) lastkey[m] = 0xffffffffu;
 
         // Row addresses: one 32 x 32 -> 64-bit multiply-add from a per-lane base.
-        const uint32_t Rb = (uint32_t)R * (uint32_t)sizeof(TF);
+        const uint32_t Rb = (uint32_t)Rin * (uint32_t)sizeof(TF);
         const char *Flb[NCH];
         const char *Fbb[NCH];
 #pragma unroll
         for (int c = 0; c < NCH; ++c) {
-            Flb[c] = reinterpret_cast<const char *>(Fl + colc[c]);
-            Fbb[c] = reinterpret_cast<const char *>(Fb + colc[c]);
+            Flb[c] = reinterpret_cast<const char *>(Fl + colL[c]);
+            Fbb[c] = reinterpret_cast<const char *>(Fb + colB[c]);
         }
 
         // ---- software pipeline over quarters of a stage (Q nonzeros; 4, or 2
@@ -658,9 +716,11 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         // the unrolled pipeline serves the 3-way SpMTTKRP and SpTTM vector
         // variants; the general-N and scalar ones walk nonzeros one at a time
         constexpr bool PIPE = (NP == 1 || NP == 2) && E > 1;
+        // first-product-mode operand: a row piece, or one element (SpTTMc)
+        using braw = typename std::conditional<KIND == 2, float, raw>::type;
         struct Quarter {
             raw cr[Q][NCH];
-            raw br[NP == 2 ? Q : 1][NCH];
+            braw br[NP == 2 ? Q : 1][NCH];
             float vv[Q];
             uint32_t fcm;
         };
@@ -711,8 +771,13 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                 if constexpr (NP == 2) {
                     const bool f = (fcm >> q) & 1u;
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c)
-                        b.br[q][c] = IO::load_if(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)jj[q] * Rb), f);
+                    for (int c = 0; c < NCH; ++c) {
+                        const TF *src = reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)jj[q] * Rb);
+                        if constexpr (KIND == 2)
+                            b.br[q][c] = f ? ld_elem(src) : 0.f;
+                        else
+                            b.br[q][c] = IO::load_if(src, f);
+                    }
                 }
             }
             b.fcm = fcm;
@@ -723,7 +788,10 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const bool f = (b.fcm >> q) & 1u;
-                    if constexpr (NP == 2) {
+                    if constexpr (NP == 2 && KIND == 2) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) brow[c][0] = f ? b.br[q][c] : brow[c][0];
+                    } else if constexpr (NP == 2) {
 #pragma unroll
                         for (int c = 0; c < NCH; ++c) {
                             float t[E];
@@ -764,7 +832,10 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                 for (int q = 0; q < Q; ++q) {
                     if ((hdm >> q) & 1u) new_segment();
                     if ((b.fcm >> q) & 1u) {
-                        if constexpr (NP == 2) {
+                        if constexpr (NP == 2 && KIND == 2) {
+#pragma unroll
+                            for (int c = 0; c < NCH; ++c) brow[c][0] = b.br[q][c];
+                        } else if constexpr (NP == 2) {
 #pragma unroll
                             for (int c = 0; c < NCH; ++c) IO::cvt(b.br[q][c], brow[c]);
                         } else if constexpr (NP != 1) {
@@ -799,7 +870,11 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                     cr[c] = IO::load(reinterpret_cast<const TF *>(Flb[c] + (uint64_t)sk[u] * Rb));
                 if (hd) new_segment();
                 if (f) {
-                    if constexpr (NP == 2) {
+                    if constexpr (NP == 2 && KIND == 2) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c)
+                            brow[c][0] = ld_elem(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sj[u] * Rb));
+                    } else if constexpr (NP == 2) {
 #pragma unroll
                         for (int c = 0; c < NCH; ++c)
                             IO::cvt(IO::load(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sj[u] * Rb)), brow[c]);
@@ -1045,6 +1120,28 @@ int launch_scalar(StreamParams &p, cudaStream_t s) {
 }
 
 bool aligned(const void *q, uintptr_t a) { return q == nullptr || ((uintptr_t)q & (a - 1)) == 0; }
+
+// SpTTMc (kind 2): output width R = Rin^nprod.  3-way tensors with Rin a
+// multiple of 8 (R = 64 or 256) take eight-column lanes, Rin = 4 (R = 16)
+// four-column lanes; every other shape the scalar lanes of the general path.
+template <typename TF>
+int launch_kron(StreamParams &p, cudaStream_t s) {
+    auto all_aligned = [&](uintptr_t a) {
+        bool ok = aligned(p.out, 16);
+        for (int m = 0; m < p.nprod; ++m) ok = ok && aligned(p.F[m], a);
+        return ok;
+    };
+    if (p.nprod == 2 && p.Rin % 8 == 0 && all_aligned(32)) {
+        if (p.R == 64) return launch_variant<TF, 8, 8, 1, 2, 2>(p, s);
+        if (p.R == 256) return launch_variant<TF, 8, 32, 1, 2, 2>(p, s);
+    }
+    if (p.nprod == 2 && p.Rin == 4 && all_aligned(16)) return launch_variant<TF, 4, 4, 1, 2, 2>(p, s);
+    const int nch = (p.R + 31) / 32;
+    if (nch <= 1) return launch_variant<TF, 1, 32, 1, 0, 2>(p, s);
+    if (nch <= 2) return launch_variant<TF, 1, 32, 2, 0, 2>(p, s);
+    if (nch <= 4) return launch_variant<TF, 1, 32, 4, 0, 2>(p, s);
+    return launch_variant<TF, 1, 32, 8, 0, 2>(p, s);
+}
 
 // Lane layout by factor type, rank and alignment: eight columns per lane
 // when R is a multiple of 8 (FP32 from R = 24 on; rows 32-byte aligned),

@@ -88,5 +88,6 @@ def test_compute_entry_points_reject_null_handles(fc):
     lib = fc.lib
     assert lib.spmttkrp(None, None, 0, 16, None, None) == -1
     assert lib.spttm(None, None, 0, 16, None, None) == -1
+    assert lib.spttmc(None, None, 0, 16, None, None) == -1
     assert b"NULL" in lib.fcoo_last_error()
     assert lib.fcoo_destroy(None) == 0
