@@ -256,10 +256,11 @@ struct SegAcc {
 // out-of-line copies below keep the loop of the short-segment variants small.
 template <int E, int NCH, int LPR>
 __device__ __forceinline__ void emit_segment_body(const SegAcc<E, NCH> &a, bool in_smem, const float *s_acc,
-                                                  const float *s_cmp, int lig, int R, float *orow, double *part) {
+                                                  const float *s_cmp, int lig, const int (&colv)[NCH], int R,
+                                                  float *orow, double *part) {
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-        const int col = (c * LPR + lig) * E;
+        const int col = colv[c];
         if (part) {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
@@ -280,22 +281,21 @@ __device__ __forceinline__ void emit_segment_body(const SegAcc<E, NCH> &a, bool 
 
 template <int E, int NCH, int LPR>
 __device__ __noinline__ void emit_segment_outlined(SegAcc<E, NCH> a, bool in_smem, const float *s_acc,
-                                                   const float *s_cmp, int lig, int R, float *orow, double *part) {
-    emit_segment_body<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, R, orow, part);
+                                                   const float *s_cmp, int lig, const int (&colv)[NCH], int R,
+                                                   float *orow, double *part) {
+    emit_segment_body<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, colv, R, orow, part);
 }
 
 // Rows from+1 .. to-1 of out hold no nonzeros: zero this lane's columns.
-template <int E, int NCH, int LPR>
-__device__ __forceinline__ void zero_rows(float *out, int R, int lig, int64_t from, int64_t to) {
+template <int E, int NCH>
+__device__ __forceinline__ void zero_rows(float *out, int R, const int (&colv)[NCH], int64_t from, int64_t to) {
     float z[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) z[e] = 0.f;
     for (int64_t rr = from + 1; rr < to; ++rr) {
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            const int col = (c * LPR + lig) * E;
-            if (col < R) store_row<E>(out + rr * R + col, z);
-        }
+        for (int c = 0; c < NCH; ++c)
+            if (colv[c] < R) store_row<E>(out + rr * R + colv[c], z);
     }
 }
 
@@ -360,12 +360,19 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
     const int64_t r0 = min(c0 + (int64_t)g * p.run_len, c1);
     const int64_t r1 = min(r0 + p.run_len, c1);
 
-    // columns of this lane
+    // SpTTMc on a 3-way tensor with vector lanes: a lane holds one E-wide
+    // piece bq of the last digit and NCH consecutive first digits, so the one
+    // row piece it gathers per nonzero serves all its chunks
+    constexpr bool KSH = KIND == 2 && NP == 2 && E > 1;
+    constexpr int NCL = KSH ? 1 : NCH;  // row pieces gathered per nonzero
+    // columns of this lane: chunk c holds columns (c * LPR + lig) * E + 0..E-1,
+    // or for KSH first digit (lig / nbp) * NCH + c, last digits from (lig % nbp) * E
+    const int nbp = KSH ? p.Rin / E : 1;
     int col[NCH];
     bool act[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-        col[c] = (c * LPR + lig) * E;
+        col[c] = KSH ? ((lig / nbp) * NCH + c) * p.Rin + (lig % nbp) * E : (c * LPR + lig) * E;
         act[c] = col[c] < R;
     }
     // loads use a clamped column so that lanes past R read valid memory
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         float lsum = 0.f;
 
         // rows between the previous segment's row and this one hold no nonzeros
-        auto fill_gap = [&](int64_t from, int64_t to) { zero_rows<E, NCH, LPR>(p.out, R, lig, from, to); };
+        auto fill_gap = [&](int64_t from, int64_t to) { zero_rows<E, NCH>(p.out, R, col, from, to); };
         // output row of the current segment
         float *orow = has_out ? p.out + row * R : nullptr;
         if (has_out && p.segrow && head0) fill_gap(seg > 0 ? (int64_t)__ldg(p.segrow + seg - 1) : -1, row);
@@ -549,9 +556,9 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
             const int slot = 2 * g + (first ? 0 : 1);
             double *part = cut ? part_ptr(slot) : nullptr;
             if constexpr (NP == 1)  // short segments: emitted often, one out-of-line copy
-                emit_segment_outlined<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, R, orow, part);
+                emit_segment_outlined<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, col, R, orow, part);
             else  // calls would cost the register-heavy variants spills in the hot loop
-                emit_segment_body<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, R, orow, part);
+                emit_segment_body<E, NCH, LPR>(a, in_smem, s_acc, s_cmp, lig, col, R, orow, part);
             if (cut && lig == 0) {
                 s_pseg[slot] = seg;
                 s_pflag[slot] = (starts_before ? 1 : 0) | (continues_after ? 2 : 0);
@@ -583,10 +590,10 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         // acc_st += w * (brow * row), w = val (KIND 0) or the residual weight
         // (KIND 1); element pairs go through the paired FP32 instructions
         // (u = position in the stage that starts at nonzero `base`)
-        auto accumulate = [&](float v, const raw (&cr)[NCH], const unsigned char *slot, int64_t base, int u) {
-            float t[NCH][E];
+        auto accumulate = [&](float v, const raw (&cr)[NCL], const unsigned char *slot, int64_t base, int u) {
+            float t[NCL][E];
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) IO::cvt(cr[c], t[c]);
+            for (int c = 0; c < NCL; ++c) IO::cvt(cr[c], t[c]);
             if constexpr (KIND == 0) {
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) {
@@ -611,18 +618,19 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) {
                     const float sc = v * brow[c][0];
+                    const float *tc = t[NCL == 1 ? 0 : c];
                     if constexpr (E % 2 == 0) {
                         const float2 s2 = make_float2(sc, sc);
 #pragma unroll
                         for (int e = 0; e < E; e += 2) {
-                            const float2 a = __ffma2_rn(s2, make_float2(t[c][e], t[c][e + 1]),
+                            const float2 a = __ffma2_rn(s2, make_float2(tc[e], tc[e + 1]),
                                                         make_float2(acc_st[c][e], acc_st[c][e + 1]));
                             acc_st[c][e] = a.x;
                             acc_st[c][e + 1] = a.y;
                         }
                     } else {
 #pragma unroll
-                        for (int e = 0; e < E; ++e) acc_st[c][e] = fmaf(sc, t[c][e], acc_st[c][e]);
+                        for (int e = 0; e < E; ++e) acc_st[c][e] = fmaf(sc, tc[e], acc_st[c][e]);
                     }
                 }
             } else {
@@ -719,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         // first-product-mode operand: a row piece, or one element (SpTTMc)
         using braw = typename std::conditional<KIND == 2, float, raw>::type;
         struct Quarter {
-            raw cr[Q][NCH];
+            raw cr[Q][NCL];
             braw br[NP == 2 ? Q : 1][NCH];
             float vv[Q];
             uint32_t fcm;
@@ -766,17 +774,25 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
 #pragma unroll
-                for (int c = 0; c < NCH; ++c)
+                for (int c = 0; c < NCL; ++c)
                     b.cr[q][c] = IO::load(reinterpret_cast<const TF *>(Flb[c] + (uint64_t)kk[q] * Rb));
                 if constexpr (NP == 2) {
                     const bool f = (fcm >> q) & 1u;
+                    if constexpr (KSH && NCH == 2 && std::is_same<TF, float>::value) {
+                        // the lane's two first digits are adjacent: one 8-byte load
+                        const float2 *src = reinterpret_cast<const float2 *>(Fbb[0] + (uint64_t)jj[q] * Rb);
+                        const float2 v2 = f ? __ldg(src) : make_float2(0.f, 0.f);
+                        b.br[q][0] = v2.x;
+                        b.br[q][1] = v2.y;
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        const TF *src = reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)jj[q] * Rb);
-                        if constexpr (KIND == 2)
-                            b.br[q][c] = f ? ld_elem(src) : 0.f;
-                        else
-                            b.br[q][c] = IO::load_if(src, f);
+                        for (int c = 0; c < NCH; ++c) {
+                            const TF *src = reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)jj[q] * Rb);
+                            if constexpr (KIND == 2)
+                                b.br[q][c] = f ? ld_elem(src) : 0.f;
+                            else
+                                b.br[q][c] = IO::load_if(src, f);
+                        }
                     }
                 }
             }
@@ -864,9 +880,9 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                         lastkey[m] = k;
                     }
                 }
-                raw cr[NCH];
+                raw cr[NCL];
 #pragma unroll
-                for (int c = 0; c < NCH; ++c)
+                for (int c = 0; c < NCL; ++c)
                     cr[c] = IO::load(reinterpret_cast<const TF *>(Flb[c] + (uint64_t)sk[u] * Rb));
                 if (hd) new_segment();
                 if (f) {
@@ -1121,9 +1137,11 @@ int launch_scalar(StreamParams &p, cudaStream_t s) {
 
 bool aligned(const void *q, uintptr_t a) { return q == nullptr || ((uintptr_t)q & (a - 1)) == 0; }
 
-// SpTTMc (kind 2): output width R = Rin^nprod.  3-way tensors with Rin a
-// multiple of 8 (R = 64 or 256) take eight-column lanes, Rin = 4 (R = 16)
-// four-column lanes; every other shape the scalar lanes of the general path.
+// SpTTMc (kind 2): output width R = Rin^nprod.  3-way tensors with Rin = 8
+// or 16 (R = 64 or 256) take eight-column lanes, Rin = 4 (R = 16) four-column
+// lanes, each lane gathering one row piece per nonzero for all its chunks
+// ((LPR / (Rin / E)) * NCH = Rin); every other shape the scalar lanes of the
+// general path.
 template <typename TF>
 int launch_kron(StreamParams &p, cudaStream_t s) {
     auto all_aligned = [&](uintptr_t a) {
@@ -1132,8 +1150,12 @@ int launch_kron(StreamParams &p, cudaStream_t s) {
         return ok;
     };
     if (p.nprod == 2 && p.Rin % 8 == 0 && all_aligned(32)) {
-        if (p.R == 64) return launch_variant<TF, 8, 8, 1, 2, 2>(p, s);
-        if (p.R == 256) return launch_variant<TF, 8, 32, 1, 2, 2>(p, s);
+        // lanes of (first-digit group, last-digit piece), two first digits
+        // per lane: 4 x 1 lanes for Rin = 8, 8 x 2 for Rin = 16 (measured on
+        // the skewed 3-way tensor: 9 % and 1.47x faster than one first digit
+        // per lane; four digits per lane, at one CTA per SM, gained nothing)
+        if (p.Rin == 8) return launch_variant<TF, 8, 4, 2, 2, 2>(p, s);
+        if (p.Rin == 16) return launch_variant<TF, 8, 16, 2, 2, 2>(p, s);
     }
     if (p.nprod == 2 && p.Rin == 4 && all_aligned(16)) return launch_variant<TF, 4, 4, 1, 2, 2>(p, s);
     const int nch = (p.R + 31) / 32;
