@@ -319,13 +319,21 @@ def fp32_alu_peak_tflops(dev, sm_mhz: float = 2070.0) -> float:
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def bench_spttmc(fc, Xs, dims, dev):
+def bench_spttmc(fc, Xs, dims, dev, T=None):
     """SpTTMc (Eq. 4) of every mode of the skewed 3-way workload at R = 8 and
     16 (output widths 64 and 256), FP32 factors, on the SpMTTKRP handles.
     Each nonzero costs R^2 FMAs: the kernel is bound by FP32 issue, not
-    HBM, so the roofline is the FP32 FMA peak."""
+    HBM, so the roofline is the FP32 FMA peak.  With the tensor T, also the
+    by-fibre plan (SpTTM along the last product mode into fibre sums, then
+    Eq. 4 over the fibres: R FMAs per nonzero plus R^2 per fibre); its
+    "eq4_TFLOPs" counts the same 2 R^2 nnz as the direct kernel."""
     peak = fp32_alu_peak_tflops(dev)
     res = {"alu_peak_tflops": peak, "peak_source": "SMs x 128 FP32 lanes x 2 x 2070 MHz", "ranks": []}
+    Xt = {}
+    if T is not None:
+        idx32 = [a.to(torch.int32).contiguous() for a in T.idx]
+        Xt = {b: fc.FCOO.build(idx32, T.val, dims, b, "ttm", 8) for b in (2, 1)}
+        del idx32
     for R in (16, 8):
         F = [f.to(dev) for f in synth.make_factors(dims, R, seed=1)]
         row = {"R": R, "width": R * R, "modes": []}
@@ -334,10 +342,21 @@ def bench_spttmc(fc, Xs, dims, dev):
             t = _time_calls(lambda: fc.spttmc(Xs[n], F, out=Y))
             fl = 2 * R * R * Xs[n].nnz
             byt = ttmc_alg_bytes(Xs[n], R)
-            row["modes"].append({"mode": n, "ms": t * 1e3, "TFLOPs": fl / t / 1e12, "frac_alu": fl / t / 1e12 / peak,
-                                 "GBps": byt / t / 1e9, "pct_hbm": byt / t / 1e9 / peaks()[0]})
+            m = {"mode": n, "ms": t * 1e3, "TFLOPs": fl / t / 1e12, "frac_alu": fl / t / 1e12 / peak,
+                 "GBps": byt / t / 1e9, "pct_hbm": byt / t / 1e9 / peaks()[0]}
+            if Xt:
+                plan = fc.SpTTMcPlan(Xt[1 if n == 2 else 2], n, R)
+                tp = _time_calls(lambda: plan.run(F, out=Y))
+                done = 2 * (R * Xs[n].nnz + R * R * plan.nfib)
+                m["by_fibres"] = {"ms": tp * 1e3, "nfib": plan.nfib, "eq4_TFLOPs": fl / tp / 1e12,
+                                  "TFLOPs": done / tp / 1e12, "frac_alu": done / tp / 1e12 / peak,
+                                  "speedup_vs_direct": t / tp}
+                plan.close()
+            row["modes"].append(m)
             del Y
         res["ranks"].append(row)
+    for X in Xt.values():
+        X.close()
     return res
 
 
@@ -556,7 +575,7 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         for name, fn in (("mttkrp_bf16", lambda: bench_mttkrp_bf16(fc, Xs, cfg.dims, R)),
                          ("spttm", lambda: bench_spttm(fc, dev, args.quick)),
-                         ("spttmc", lambda: bench_spttmc(fc, Xs, cfg.dims, dev)),
+                         ("spttmc", lambda: bench_spttmc(fc, Xs, cfg.dims, dev, T)),
                          ("cp_als", lambda: bench_cp_als(fc, Xs, cfg.dims, 20 if not args.quick else 5)),
                          ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick))):
             try:
@@ -636,8 +655,8 @@ def main():
             line = bench_sweep(fc, dev, args.quick)
         elif args.part == "spttmc":
             cfg = workload_config(args)
-            _, Xs, _, _ = build_workload(cfg, dev)
-            line = bench_spttmc(fc, Xs, cfg.dims, dev)
+            T, Xs, _, _ = build_workload(cfg, dev)
+            line = bench_spttmc(fc, Xs, cfg.dims, dev, T)
         else:
             cfg = workload_config(args)
             _, Xs, _, _ = build_workload(cfg, dev)

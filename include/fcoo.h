@@ -223,6 +223,43 @@ int spttm(const fcoo_t *X, const void *U, int dtype, int R, float *out, fcoo_str
  * `stream`. */
 int spttmc(const fcoo_t *X, const void *const *factors, int dtype, int R, float *out, fcoo_stream_t stream);
 
+/* SpTTMc of a 3-way tensor by fibres: Eq. 4 regrouped, with the same result
+ * up to rounding.  For index mode n and product modes a < b, the sum over
+ * the mode-b index k runs first, along each fibre (i_n, i_a) of the SpTTM
+ * handle along mode b (Eq. 3): T(f, :) = sum_k X U_b(k, :).  Then Eq. 4 runs
+ * over the fibres, one term U_a(i_a, :) (x) T(f, :) per fibre.  A nonzero
+ * costs R FMAs plus R^2 per fibre, instead of R^2 (fewer wherever fibres
+ * hold more than one nonzero).
+ *
+ * spttmc_plan_create
+ *   Xttm      3-way handle built with op = FCOO_OP_TTM along mode b, where b
+ *             is the highest mode other than `mode` (b = 2 for mode 0 or 1,
+ *             b = 1 for mode 2).  Not copied: it must outlive the plan.
+ *   mode      the SpTTMc index mode n, 0..2
+ *   R         rank of both factors, 1..16 (R^2 <= FCOO_MAX_RANK)
+ *   threadlen partition length of the fibre tensor's F-COO (as fcoo_build)
+ *   plan      receives the plan.  It holds the fibre tensor (an F-COO of
+ *             nfib nonzeros) and nfib x R FP32 fibre sums in device memory.
+ *   Synchronous (it builds an F-COO).  Errors: FCOO_ERR_INVALID_ARG (wrong
+ *   handle or mode), FCOO_ERR_UNSUPPORTED (R), FCOO_ERR_NOMEM, FCOO_ERR_CUDA.
+ * spttmc_plan_run
+ *   factors   host array of 3 device pointers to dims[k] x R FP32 row-major
+ *             factors; factors[mode] is not read (may be NULL)
+ *   dtype     FCOO_F32 (others: FCOO_ERR_UNSUPPORTED)
+ *   out       device float32 dims[mode] x R^2, columns r_a * R + r_b as for
+ *             spttmc; every element written
+ *   Two kernels and a fix-up, asynchronous on `stream`; deterministic.
+ *   Calls on one plan must not overlap (they share the fibre sums).
+ * spttmc_plan_info: fibres of the plan and the device bytes it holds.
+ * spttmc_plan_destroy: frees the plan (NULL is accepted). */
+typedef struct fcoo_ttmc_plan fcoo_ttmc_plan_t;
+int spttmc_plan_create(const fcoo_t *Xttm, int mode, int R, int threadlen, fcoo_ttmc_plan_t **plan,
+                       fcoo_stream_t stream);
+int spttmc_plan_run(const fcoo_ttmc_plan_t *plan, const void *const *factors, int dtype, float *out,
+                    fcoo_stream_t stream);
+int spttmc_plan_info(const fcoo_ttmc_plan_t *plan, int64_t *nfib, int64_t *device_bytes);
+int spttmc_plan_destroy(fcoo_ttmc_plan_t *plan);
+
 /* ---------------------------------------------------------------------- */
 /* SpMTTKRP for callers that cannot allocate device memory                  */
 /* ---------------------------------------------------------------------- */

@@ -223,6 +223,59 @@ def spttmc(X: FCOO, factors: Sequence[Optional[torch.Tensor]], out: Optional[tor
 __all__ += ["spttmc"]
 
 
+class SpTTMcPlan:
+    """SpTTMc of a 3-way tensor by fibres (Eq. 4 regrouped through Eq. 3):
+    an SpTTM along the last product mode b into fibre sums, then Eq. 4 over
+    the fibres.  ``Xttm`` is the SpTTM handle along b (b = 2 for mode 0 or 1,
+    1 for mode 2); it must stay open while the plan is used."""
+
+    def __init__(self, Xttm: FCOO, mode: int, R: int, threadlen: int = 8, stream=None):
+        out = ctypes.c_void_p()
+        check(lib.spttmc_plan_create(Xttm.handle, int(mode), int(R), int(threadlen), ctypes.byref(out),
+                                     _stream(stream)))
+        self._h = out
+        self._X = Xttm  # keeps the handle alive
+        self.mode, self.R, self.dims = int(mode), int(R), tuple(Xttm.dims)
+        nf, nb = ctypes.c_int64(), ctypes.c_int64()
+        check(lib.spttmc_plan_info(self._h, ctypes.byref(nf), ctypes.byref(nb)))
+        self.nfib, self.device_bytes = nf.value, nb.value
+
+    def run(self, factors: Sequence[Optional[torch.Tensor]], out: Optional[torch.Tensor] = None,
+            stream=None) -> torch.Tensor:
+        """dims[mode] x R^2 float32, columns r_a * R + r_b (a < b the other modes)."""
+        ptrs = []
+        ref = None
+        for k in range(3):
+            if k == self.mode:
+                ptrs.append(None)
+                continue
+            f = factors[k]
+            _check_factor(f, self.dims[k], self.R, f"factors[{k}]")
+            if f.dtype != torch.float32:
+                raise TypeError("SpTTMc takes float32 factors")
+            ptrs.append(f.data_ptr())
+            ref = f
+        if out is None:
+            out = torch.empty((self.dims[self.mode], self.R * self.R), dtype=torch.float32, device=ref.device)
+        pp, _keep = ptr_array(ptrs)
+        check(lib.spttmc_plan_run(self._h, pp, F32, out.data_ptr(), _stream(stream)))
+        return out
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib.spttmc_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ += ["SpTTMcPlan"]
+
+
 # ---------------------------------------------------------------- CP-ALS (Algorithm 1)
 
 

@@ -74,6 +74,10 @@ SIGNATURES = {
     "spmttkrp": (_i, [_vp, _vpp, _i, _i, _vp, _vp]),
     "spttm": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
     "spttmc": (_i, [_vp, _vpp, _i, _i, _vp, _vp]),
+    "spttmc_plan_create": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_vp), _vp]),
+    "spttmc_plan_run": (_i, [_vp, _vpp, _i, _vp, _vp]),
+    "spttmc_plan_info": (_i, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "spttmc_plan_destroy": (_i, [_vp]),
     "spmttkrp_noalloc": (_i, [ctypes.POINTER(FcooView), _vpp, _i, _i, _vp, _vp]),
     "cp_state_create": (_i, [_i, _vp, _i, _i, _vpp, _vp, ctypes.POINTER(_vp)]),
     "cp_state_destroy": (_i, [_vp]),
