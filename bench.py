@@ -374,9 +374,10 @@ def _time_calls(fn, n=20, warm=3):
 
 
 def bench_sweep(fc, dev, quick):
-    """Mode and rank sweep: SpTTM along every mode of the 4-way workload
-    (R = 16) and SpMTTKRP of every mode of the skewed 3-way workload at
-    R = 8, 16, 32, 64 (FP32 factors).  GB/s of algorithmic bytes per call."""
+    """Mode, rank and threadlen sweep: SpTTM along every mode of the 4-way
+    workload (R = 16), SpMTTKRP of every mode of the skewed 3-way workload at
+    R = 8, 16, 32, 64 (FP32 factors), and SpMTTKRP mode 0 at R = 32 for
+    threadlen 1..64.  GB/s of algorithmic bytes per call."""
     out = {"spttm_modes": [], "spmttkrp_ranks": []}
     cfg = synth.CONFIGS["ttm4"]
     if quick:
@@ -396,7 +397,21 @@ def bench_sweep(fc, dev, quick):
     del T, idx32
     cfg = synth.CONFIGS["skewed3"] if not quick else synth.scaled(synth.CONFIGS["skewed3"], 4_000_000,
                                                                  dims=(1200, 900, 2800))
-    _, Xs, _, _ = build_workload(cfg, dev)
+    T, Xs, _, _ = build_workload(cfg, dev)
+    # threadlen (the partition length of the start-flags, tuned per tensor in
+    # the paper's Table IV): SpMTTKRP mode 0 at R = 32 on handles built with
+    # each value
+    out["spmttkrp_threadlen"] = []
+    idx32 = [a.to(torch.int32).contiguous() for a in T.idx]
+    F = [f.to(dev) for f in synth.make_factors(cfg.dims, 32, seed=1)]
+    M = torch.empty((cfg.dims[0], 32), device=dev)
+    for tl in (1, 4, 8, 16, 32, 64):
+        X = fc.FCOO.build(idx32, T.val, cfg.dims, 0, "mttkrp", tl)
+        t = _time_calls(lambda: fc.spmttkrp(X, F, out=M))
+        byt = mttkrp_alg_bytes(X, 32, 4)
+        out["spmttkrp_threadlen"].append({"threadlen": tl, "ms": t * 1e3, "GBps": byt / t / 1e9})
+        X.close()
+    del idx32, T, M
     for R in (8, 16, 32, 64):
         F = [f.to(dev) for f in synth.make_factors(cfg.dims, R, seed=1)]
         row = {"R": R, "modes": []}
