@@ -13,6 +13,7 @@ for the passage of the paper each routine follows:
 * ``mttkrp``        -- Eq. 5 / Eq. 6, Table I row 2 (SpMTTKRP on mode n)
 * ``ttm``           -- Eq. 3, Table I row 1 (SpTTM, semi-sparse output)
 * ``ttmc``          -- Eq. 4, Table I row 3 (SpTTMc, dense Kronecker-row output)
+* ``hooi``          -- Tucker by HOOI around SpTTMc (Sec. II), numpy SVD per mode
 * ``fcoo_layout``   -- Sec. IV-B, Table I, Fig. 2 caption (sort order, flags)
 * ``cp_als``        -- Algorithm 1 (CP-ALS), N-way
 * ``spd_solve``     -- the ``V^dagger`` of Algorithm 1 (Cholesky / pinv)
@@ -268,3 +269,48 @@ def cp_fit(dims, idx, val, factors, lam):
     lam = _f64(lam)
     return float(lib.orc_cp_fit(c.nmodes, c.dims_ptr, ctypes.c_int64(c.nnz), c.idx_ptrs, val.ctypes.data_as(_f64p),
                                 int(fs[0].shape[1]), _ptr_table(fs), lam.ctypes.data_as(_f64p)))
+
+
+def sign_fix(U):
+    """Column sign convention shared by the Tucker factors of both sides:
+    each column's entry of largest magnitude (the first, on ties) is made
+    positive.  Singular vectors are defined only up to sign."""
+    U = np.array(U, dtype=np.float64, copy=True)
+    for r in range(U.shape[1]):
+        i = int(np.argmax(np.abs(U[:, r])))
+        if U[i, r] < 0:
+            U[:, r] = -U[:, r]
+    return U
+
+
+def hooi_mode(dims, idx, val, factors, n, R):
+    """One HOOI factor update (Sec. II; Eq. 4 as its TTM chain): Y_(n) =
+    SpTTMc of mode n with the other factors, then the R leading left singular
+    vectors of Y_(n) (numpy SVD), sign-fixed.  Returns (U_n, sigma^2 of the
+    R leading singular values)."""
+    Y = ttmc(dims, idx, val, factors, n)
+    U, s, _ = np.linalg.svd(Y, full_matrices=False)
+    k = min(R, U.shape[1])
+    Un = np.zeros((int(dims[n]), R))
+    Un[:, :k] = U[:, :k]
+    sig2 = np.zeros(R)
+    sig2[:k] = s[:k] ** 2
+    return sign_fix(Un), sig2
+
+
+def hooi(dims, idx, val, init_factors, iters):
+    """Tucker decomposition by higher-order orthogonal iteration: `iters`
+    sweeps over the modes in order, each mode replaced by hooi_mode with the
+    latest factors.  The core is G = Y_(N-1) times U_(N-1)^T, so |G|^2 is the
+    sum of the last mode's sigma^2, and fit = 1 - sqrt(max(0, |X|^2 -
+    |G|^2)) / |X| (the factors are orthonormal).  Returns (factors, fits)."""
+    F = [np.array(f, dtype=np.float64) for f in init_factors]
+    R = F[0].shape[1]
+    x2 = float(np.sum(np.asarray(val, dtype=np.float64) ** 2))
+    fits = []
+    for _ in range(iters):
+        for n in range(len(dims)):
+            F[n], sig2 = hooi_mode(dims, idx, val, F, n, R)
+        g2 = float(np.sum(sig2))
+        fits.append(1.0 - np.sqrt(max(0.0, x2 - g2)) / np.sqrt(x2))
+    return F, fits

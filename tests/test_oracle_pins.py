@@ -16,7 +16,10 @@ fit formula) fails at least one of them:
 * Algorithm 1: fit never decreases, fit formula equals the dense residual,
   one sweep equals a numpy pinv re-derivation, exact recovery of a low-rank
   tensor, pseudo-inverse fallback against numpy.linalg.pinv;
-* sparse-fit gradients against central finite differences, adjoint identity.
+* sparse-fit gradients against central finite differences, adjoint identity;
+* HOOI: exact recovery of a tensor of multilinear rank (2, 2, 2), orthonormal
+  factors, a fit that never decreases and equals the dense residual of the
+  projected tensor.
 """
 import json
 import os
@@ -294,6 +297,52 @@ def test_ttmc_single_nonzero_and_empty(oracle):
     np.testing.assert_array_equal(Y, ref)
     empty = [np.zeros(0, np.uint32)] * 3
     np.testing.assert_array_equal(oracle.ttmc(dims, empty, np.zeros(0), U, 0), np.zeros((3, 4)))
+
+
+# ---------------------------------------------------------------- Tucker (HOOI)
+
+
+def orthonormal(rng, n, r):
+    q, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    return q
+
+
+def test_hooi_recovers_exact_multilinear_rank(oracle):
+    # X = G x1 A x2 B x3 C with orthonormal A, B, C: one sweep from a random
+    # start finds span(A), span(B), span(C) and fit 1
+    rng = np.random.default_rng(31)
+    dims, R = (8, 7, 6), 2
+    A, B, C = (orthonormal(rng, d, R) for d in dims)
+    G = rng.standard_normal((R, R, R))
+    X = np.einsum("abc,ia,jb,kc->ijk", G, A, B, C)
+    idx = [a.astype(np.uint32).ravel() for a in np.indices(dims)]
+    init = [rng.standard_normal((d, R)) for d in dims]
+    F, fits = oracle.hooi(dims, idx, X.ravel(), init, 2)
+    assert abs(fits[0] - 1.0) < 1e-7 and abs(fits[1] - 1.0) < 1e-7
+    for Un, T in zip(F, (A, B, C)):
+        np.testing.assert_allclose(Un @ Un.T, T @ T.T, atol=1e-10)
+
+
+def test_hooi_orthonormal_monotone_and_core_identity(oracle):
+    rng = np.random.default_rng(32)
+    dims, R = (12, 10, 9), 3
+    idx, val = rand_coo(rng, dims, 300)
+    init = [rng.standard_normal((d, R)) for d in dims]
+    F, fits = oracle.hooi(dims, idx, val, init, 6)
+    for Un in F:
+        np.testing.assert_allclose(Un.T @ Un, np.eye(R), atol=1e-12)
+    assert all(b >= a - 1e-12 for a, b in zip(fits, fits[1:]))
+    # the fit from the singular values equals the dense residual of the
+    # projection X x_k U_k U_k^T
+    X = densify(dims, idx, val)
+    Gc = np.einsum("ijk,ia,jb,kc->abc", X, *F)
+    Xh = np.einsum("abc,ia,jb,kc->ijk", Gc, *F)
+    fit_dense = 1.0 - np.linalg.norm(X - Xh) / np.linalg.norm(X)
+    assert abs(fits[-1] - fit_dense) < 1e-10
+    # each factor's columns are signed so that their largest entry is positive
+    for Un in F:
+        for r in range(R):
+            assert Un[np.argmax(np.abs(Un[:, r])), r] > 0
 
 
 # ---------------------------------------------------------------- F-COO layout
