@@ -360,6 +360,25 @@ def bench_spttmc(fc, Xs, dims, dev, T=None):
     return res
 
 
+def bench_tucker(fc, Xs, dims, R=8, iters=5):
+    """Tucker (HOOI around SpTTMc) on the skewed 3-way workload, rank
+    (R, R, R): seconds per iteration over `iters` iterations after one
+    untimed iteration from N(0,1) start factors."""
+    g = torch.Generator().manual_seed(4)
+    st = fc.TuckerState(dims, R, [torch.randn(d, R, generator=g) for d in dims])
+    st.iterate(Xs, 1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    st.iterate(Xs, iters)
+    b.record()
+    torch.cuda.synchronize()
+    s = st.stats()
+    st.close()
+    return {"R": R, "iters_timed": iters, "ms_per_iter": a.elapsed_time(b) / iters, "fit": s["fit"],
+            "null_directions": s["null_directions"]}
+
+
 def _time_calls(fn, n=20, warm=3):
     for _ in range(warm):
         fn()
@@ -591,6 +610,7 @@ def run_ours(args):
         for name, fn in (("mttkrp_bf16", lambda: bench_mttkrp_bf16(fc, Xs, cfg.dims, R)),
                          ("spttm", lambda: bench_spttm(fc, dev, args.quick)),
                          ("spttmc", lambda: bench_spttmc(fc, Xs, cfg.dims, dev, T)),
+                         ("tucker", lambda: bench_tucker(fc, Xs, cfg.dims)),
                          ("cp_als", lambda: bench_cp_als(fc, Xs, cfg.dims, 20 if not args.quick else 5)),
                          ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick))):
             try:
@@ -651,9 +671,10 @@ def main():
     ap.add_argument("--rank", type=int, default=0, help="override R")
     ap.add_argument("--cpu-sample", type=int, default=40_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
-    ap.add_argument("--part", default="all", choices=["all", "spttm", "spttmc", "cp", "fit", "sweep"],
+    ap.add_argument("--part", default="all", choices=["all", "spttm", "spttmc", "tucker", "cp", "fit", "sweep"],
                     help="only one extra line, for profiling: spttm (4-way workload, --nnz scales it), "
                          "spttmc (SpTTMc of every mode of the skewed 3-way workload, R = 8 and 16), "
+                         "tucker (HOOI at R = 8 on the skewed 3-way workload), "
                          "cp (CP-ALS on the skewed 3-way workload), fit (sparse CP fit) or sweep "
                          "(SpTTM along every mode, SpMTTKRP at R = 8..64)")
     ap.add_argument("--sweeps", type=int, default=20, help="CP-ALS sweeps of the cp line")
@@ -668,10 +689,15 @@ def main():
             line = bench_sparse_fit(fc, dev, args.quick)
         elif args.part == "sweep":
             line = bench_sweep(fc, dev, args.quick)
+        elif args.part == "tucker":
+            cfg = workload_config(args)
+            _, Xs, _, _ = build_workload(cfg, dev)
+            line = bench_tucker(fc, Xs, cfg.dims, iters=args.sweeps if args.sweeps != 20 else 5)
         elif args.part == "spttmc":
             cfg = workload_config(args)
             T, Xs, _, _ = build_workload(cfg, dev)
             line = bench_spttmc(fc, Xs, cfg.dims, dev, T)
+            line["tucker"] = bench_tucker(fc, Xs, cfg.dims)
         else:
             cfg = workload_config(args)
             _, Xs, _, _ = build_workload(cfg, dev)

@@ -261,6 +261,46 @@ int spttmc_plan_info(const fcoo_ttmc_plan_t *plan, int64_t *nfib, int64_t *devic
 int spttmc_plan_destroy(fcoo_ttmc_plan_t *plan);
 
 /* ---------------------------------------------------------------------- */
+/* Tucker decomposition by HOOI around SpTTMc (Sec. II: HOOI's key          */
+/* operation is TTMc, Eq. 4)                                                */
+/* ---------------------------------------------------------------------- */
+
+/* State of a rank-(R, ..., R) Tucker decomposition: N factors U_k (dims[k] x
+ * R, FP32, device).  One iteration (tucker_hooi_iter) updates the modes in
+ * order; mode n's update is
+ *   Y_(n) = SpTTMc of mode n with the current other factors (dims[n] x W,
+ *           W = R^(N-1)),
+ *   U_n   = the R leading left singular vectors of Y_(n): eigenvectors q_r of
+ *           S = Y^T Y (FP64 Gram of compensated FP32 partials; FP32 parallel
+ *           Jacobi) mapped back as Y q_r / sqrt(d_r), each column signed so
+ *           that its entry of largest magnitude (first row on ties) is
+ *           positive.
+ * After the last mode, |G|^2 = sum_r q_r^T S q_r (the core's squared norm)
+ * and fit = 1 - sqrt(max(0, |X|^2 - |G|^2)) / |X|.  A direction whose
+ * eigenvalue is below 1e-6 of the largest leaves a zero column and is
+ * counted (nnull in tucker_state_stats).
+ *
+ * tucker_state_create
+ *   nmodes 2..FCOO_MAX_MODES; dims host array; R 1..12 with R^(N-1) <= 128
+ *   (FCOO_ERR_UNSUPPORTED above); init: N pointers (host or device) to
+ *   dims[k] x R FP32 start factors (copied).  Synchronous.
+ * tucker_hooi_iter
+ *   Xn: N SpMTTKRP handles of one tensor, Xn[n] built for mode n.  About
+ *   seven launches per mode, asynchronous on `stream`; deterministic.
+ * tucker_state_stats: fit, |G|^2, iterations done, null directions met
+ *   (synchronous; any pointer may be NULL).
+ * tucker_state_copy_factor: U_n to host or device memory (synchronous).
+ * tucker_state_destroy: frees the state (NULL is accepted). */
+typedef struct tucker_state tucker_state_t;
+int tucker_state_create(int nmodes, const uint32_t *dims, int R, const float *const *init, fcoo_stream_t stream,
+                        tucker_state_t **out);
+int tucker_hooi_iter(const fcoo_t *const *Xn, tucker_state_t *st, fcoo_stream_t stream);
+int tucker_state_stats(const tucker_state_t *st, double *fit, double *core_sq, int *iters, int *nnull,
+                       fcoo_stream_t stream);
+int tucker_state_copy_factor(const tucker_state_t *st, int n, float *dst, fcoo_stream_t stream);
+int tucker_state_destroy(tucker_state_t *st);
+
+/* ---------------------------------------------------------------------- */
 /* SpMTTKRP for callers that cannot allocate device memory                  */
 /* ---------------------------------------------------------------------- */
 

@@ -366,6 +366,66 @@ class CPState:
 __all__ += ["CPState"]
 
 
+class TuckerState:
+    """Device state of a rank-(R, ..., R) Tucker decomposition driven by
+    ``tucker_hooi_iter`` (HOOI around SpTTMc, Eq. 4)."""
+
+    def __init__(self, dims: Sequence[int], R: int, init: Sequence, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.R = int(R)
+        keep, ptrs = [], []
+        for k, f in enumerate(init):
+            if isinstance(f, torch.Tensor):
+                t = f.detach().to(torch.float32).contiguous()
+                if not t.is_cuda:
+                    t = t.numpy()
+            else:
+                t = np.ascontiguousarray(np.asarray(f, dtype=np.float32))
+            if tuple(t.shape) != (self.dims[k], self.R):
+                raise ValueError(f"init[{k}] must be {self.dims[k]}x{self.R}")
+            keep.append(t)
+            ptrs.append(t.data_ptr() if isinstance(t, torch.Tensor) else t.ctypes.data)
+        dims_arr = (ctypes.c_uint32 * len(self.dims))(*self.dims)
+        pp, _pk = ptr_array(ptrs)
+        out = ctypes.c_void_p()
+        check(lib.tucker_state_create(len(self.dims), ctypes.cast(dims_arr, ctypes.c_void_p), self.R, pp,
+                                      _stream(stream), ctypes.byref(out)))
+        self._h = out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.tucker_state_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self, Xn: Sequence[FCOO], iters: int = 1, stream=None):
+        """Run ``iters`` HOOI iterations (asynchronous on the stream)."""
+        hs = (ctypes.c_void_p * len(Xn))(*[x.handle.value for x in Xn])
+        for _ in range(int(iters)):
+            check(lib.tucker_hooi_iter(ctypes.cast(hs, ctypes.POINTER(ctypes.c_void_p)), self._h, _stream(stream)))
+        return self
+
+    def stats(self, stream=None) -> dict:
+        fit, g2 = ctypes.c_double(), ctypes.c_double()
+        it, nnull = ctypes.c_int(), ctypes.c_int()
+        check(lib.tucker_state_stats(self._h, ctypes.byref(fit), ctypes.byref(g2), ctypes.byref(it),
+                                     ctypes.byref(nnull), _stream(stream)))
+        return {"fit": fit.value, "core_sq": g2.value, "iters": it.value, "null_directions": nnull.value}
+
+    def factor(self, n: int, stream=None) -> np.ndarray:
+        out = np.empty((self.dims[n], self.R), dtype=np.float32)
+        check(lib.tucker_state_copy_factor(self._h, int(n), out.ctypes.data, _stream(stream)))
+        return out
+
+
+__all__ += ["TuckerState"]
+
+
 # ---------------------------------------------------------------- differentiation
 
 

@@ -80,6 +80,11 @@ SIGNATURES = {
     "spttmc_plan_destroy": (_i, [_vp]),
     "spmttkrp_noalloc": (_i, [ctypes.POINTER(FcooView), _vpp, _i, _i, _vp, _vp]),
     "cp_state_create": (_i, [_i, _vp, _i, _i, _vpp, _vp, ctypes.POINTER(_vp)]),
+    "tucker_state_create": (_i, [_i, _vp, _i, _vpp, _vp, ctypes.POINTER(_vp)]),
+    "tucker_state_destroy": (_i, [_vp]),
+    "tucker_hooi_iter": (_i, [_vpp, _vp, _vp]),
+    "tucker_state_stats": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "tucker_state_copy_factor": (_i, [_vp, _i, _vp, _vp]),
     "cp_state_destroy": (_i, [_vp]),
     "cp_als_iter": (_i, [_vpp, _vp, _vp]),
     "cp_state_stats": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),

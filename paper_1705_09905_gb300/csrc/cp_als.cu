@@ -721,6 +721,27 @@ int mode_update(const fcoo_t *X, cp_state_t *st, int n, bool last, cudaStream_t 
 }
 
 }  // namespace
+
+// Helpers shared with the Tucker solver (tucker.cu).
+int gram_f32_fp64(const float *F, int64_t I, int R, double *part, double *G, cudaStream_t s) {
+    const int nb = (int)ceil_div(I, kRowsPerBlock);
+    const size_t smem = (size_t)kRowsPerBlock * R * 4;
+    FCOO_CUDA(cudaFuncSetAttribute(k_gram_part<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_gram_part<float><<<nb, 256, smem, s>>>(F, I, R, part);
+    FCOO_CUDA(cudaGetLastError());
+    k_gram_reduce<<<(unsigned)ceil_div(R * R, 32), 256, 0, s>>>(part, nb, R, G);
+    FCOO_CUDA(cudaGetLastError());
+    return FCOO_OK;
+}
+
+int sumsq_fp64(const float *val, int64_t n, double *part, double *out, cudaStream_t s) {
+    const int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, ceil_div(n, 256)));
+    k_sumsq_part<<<nb, 256, 0, s>>>(val, n, part);
+    k_sum_final<<<1, 256, 0, s>>>(part, nb, out);
+    FCOO_CUDA(cudaGetLastError());
+    return FCOO_OK;
+}
+
 }  // namespace fcx
 
 using namespace fcx;

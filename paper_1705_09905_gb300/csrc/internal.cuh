@@ -132,4 +132,11 @@ int launch_stream_bf16_k0(StreamParams &p, cudaStream_t s);
 int launch_stream_bf16_k1(StreamParams &p, cudaStream_t s);
 int launch_stream_f32_k2(StreamParams &p, cudaStream_t s);
 
+// G = F^T F (R x R, FP64) of an I x R FP32 matrix: compensated (Dot2) FP32
+// partials over 128-row blocks (part: ceil(I/128) * R * R doubles), summed in
+// FP64 (cp_als.cu).  R <= 128.
+int gram_f32_fp64(const float *F, int64_t I, int R, double *part, double *G, cudaStream_t s);
+// *out = sum of val[p]^2 in FP64 (part: 1024 doubles).
+int sumsq_fp64(const float *val, int64_t n, double *part, double *out, cudaStream_t s);
+
 }  // namespace fcx

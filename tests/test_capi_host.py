@@ -92,6 +92,9 @@ def test_compute_entry_points_reject_null_handles(fc):
     assert lib.spttmc_plan_create(None, 0, 8, 8, None, None) == -1
     assert lib.spttmc_plan_run(None, None, 0, None, None) == -1
     assert lib.spttmc_plan_info(None, None, None) == -1
+    assert lib.tucker_hooi_iter(None, None, None) == -1
+    assert lib.tucker_state_stats(None, None, None, None, None, None) == -1
+    assert lib.tucker_state_copy_factor(None, 0, None, None) == -1
     assert b"NULL" in lib.fcoo_last_error()
     assert lib.spttmc_plan_destroy(None) == 0
     assert lib.fcoo_destroy(None) == 0
