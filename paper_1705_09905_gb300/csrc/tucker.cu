@@ -29,6 +29,8 @@ struct tucker_state {
     double *S;                 // W x W
     double *Qd;                // W x W eigenvectors (columns)
     double *T1, *Aq;           // W x W: S Q1 and Q1^T S Q1
+    double *Qprev[FCOO_MAX_MODES];  // W x W: each mode's last eigenvectors (warm start)
+    bool have_q[FCOO_MAX_MODES];
     double *part;              // Gram partials / |X|^2 partials
     float *cand;               // per-block sign candidates: [nb][R][3] (|u|, index, u)
     int *sel;                  // R selected eigenpairs
@@ -54,15 +56,18 @@ constexpr int kProjWarps = 8;    // rows in flight per projection CTA
 // Each step rotates W/2 disjoint pairs at once (round-robin ordering: one
 // index fixed, the others on a circle), so the rotations commute and
 // A <- J^T A J is two passes over the pairs.  Rotation angles are taken in
-// FP64.  Stops when the off-diagonal entries are at the rounding level of TA
+// TA.  Stops when the off-diagonal entries are at the rounding level of TA
 // (|a_pq| ~ 8 eps |A|_F), or, once near it, when a sweep gains less than 4x;
-// at most max_sweeps.  Returns the sweeps done (thread 0).
+// at most max_sweeps.  With `act` (shared flags, one per index), only pairs
+// with an active index rotate and only their entries count as off-diagonal:
+// the leading eigenvectors are refined without touching the rest of the
+// spectrum.  Returns the sweeps done.
 template <typename TA, typename TQ>
-__device__ int jacobi_sweeps(TA *A, TQ *Q, int W, int max_sweeps, double eps) {
-    __shared__ double s_c[kMaxW / 2 + 1], s_s[kMaxW / 2 + 1];
+__device__ int jacobi_sweeps(TA *A, TQ *Q, int W, int max_sweeps, double eps, const int *act) {
+    __shared__ TA s_c[kMaxW / 2 + 1], s_s[kMaxW / 2 + 1];
     __shared__ int s_p[kMaxW / 2 + 1], s_q[kMaxW / 2 + 1];
     __shared__ double s_red[kEigThreads / 32][2];
-    __shared__ int s_done;
+    __shared__ int s_done, s_np, s_wc[2];
     __shared__ double s_prev;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) s_prev = -1.0;
@@ -73,8 +78,9 @@ __device__ int jacobi_sweeps(TA *A, TQ *Q, int W, int max_sweeps, double eps) {
         double off = 0.0, tot = 0.0;
         for (int e = tid; e < W * W; e += nt) {
             const double a = A[e];
+            const int i = e / W, j = e % W;
             tot += a * a;
-            if (e / W != e % W) off += a * a;
+            if (i != j && (!act || act[i] || act[j])) off += a * a;
         }
         for (int o = 16; o > 0; o >>= 1) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
@@ -100,7 +106,12 @@ __device__ int jacobi_sweeps(TA *A, TQ *Q, int W, int max_sweeps, double eps) {
         if (s_done) break;
         ++sweeps;
         for (int step = 0; step < m - 1; ++step) {
-            for (int k = tid; k < half; k += nt) {
+            // threads k < half (two warps at most) each take pair k of this step
+            bool rot = false;
+            int p = -1, q = -1;
+            TA c = 1, sn = 0;
+            if (tid < half) {
+                const int k = tid;
                 int a, b;
                 if (k == 0) {
                     a = m - 1;
@@ -109,42 +120,65 @@ __device__ int jacobi_sweeps(TA *A, TQ *Q, int W, int max_sweeps, double eps) {
                     a = (step + k) % (m - 1);
                     b = (step - k + m - 1) % (m - 1);
                 }
-                int p = min(a, b), q = max(a, b);
-                double c = 1.0, sn = 0.0;
-                if (q < W) {
-                    const double apq = A[p * W + q];
-                    if (apq != 0.0) {
-                        const double theta = ((double)A[q * W + q] - (double)A[p * W + p]) / (2.0 * apq);
-                        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                        c = 1.0 / sqrt(t * t + 1.0);
+                p = min(a, b);
+                q = max(a, b);
+                if (q < W && (!act || act[p] || act[q])) {
+                    const TA apq = A[p * W + q];
+                    if (apq != (TA)0) {
+                        const TA theta = (A[q * W + q] - A[p * W + p]) / (2 * apq);
+                        const TA at = theta >= 0 ? theta : -theta;
+                        // t = tan of the rotation angle (the smaller root)
+                        const TA t = at > (TA)1e15 ? (TA)0.5 / theta
+                                                   : (theta >= 0 ? (TA)1 : (TA)-1) / (at + sqrt(theta * theta + 1));
+                        c = 1 / sqrt(t * t + 1);
                         sn = t * c;
+                        rot = true;
                     }
-                } else {
-                    p = q = -1;  // the dummy index of an odd W
                 }
-                s_c[k] = c;
-                s_s[k] = sn;
-                s_p[k] = p;
-                s_q[k] = q;
+            }
+            if (!act) {
+                // every pair in its slot; the update passes skip the idle ones
+                if (tid < half) {
+                    s_c[tid] = c;
+                    s_s[tid] = sn;
+                    s_p[tid] = rot ? p : -1;
+                    s_q[tid] = q;
+                }
+            } else if (tid < 64) {
+                // pack the rotating pairs (warp ballots; order kept)
+                const unsigned bal = __ballot_sync(0xffffffffu, rot);
+                if ((tid & 31) == 0) s_wc[tid >> 5] = __popc(bal);
+                __syncwarp();
+                asm volatile("bar.sync 1, 64;" ::: "memory");  // the two warps of the pair threads
+                const int base = (tid >> 5) ? s_wc[0] : 0;
+                const int pos = base + __popc(bal & ((1u << (tid & 31)) - 1u));
+                if (rot) {
+                    s_c[pos] = c;
+                    s_s[pos] = sn;
+                    s_p[pos] = p;
+                    s_q[pos] = q;
+                }
+                if (tid == 0) s_np = s_wc[0] + s_wc[1];
             }
             __syncthreads();
+            const int np = act ? s_np : half;
             // A <- A J (columns p, q of every row)
-            for (int e = tid; e < W * half; e += nt) {
-                const int r = e / half, k = e % half;
+            for (int e = tid; e < W * np; e += nt) {
+                const int r = e / np, k = e % np;
                 const int p = s_p[k], q = s_q[k];
-                if (p < 0 || s_s[k] == 0.0) continue;
-                const TA c = (TA)s_c[k], sn = (TA)s_s[k];
+                if (p < 0 || s_s[k] == (TA)0) continue;
+                const TA c = s_c[k], sn = s_s[k];
                 const TA ap = A[r * W + p], aq = A[r * W + q];
                 A[r * W + p] = c * ap - sn * aq;
                 A[r * W + q] = sn * ap + c * aq;
             }
             __syncthreads();
             // A <- J^T A (rows p, q), Q <- Q J
-            for (int e = tid; e < W * half; e += nt) {
-                const int col = e / half, k = e % half;
+            for (int e = tid; e < W * np; e += nt) {
+                const int col = e / np, k = e % np;
                 const int p = s_p[k], q = s_q[k];
-                if (p < 0 || s_s[k] == 0.0) continue;
-                const TA c = (TA)s_c[k], sn = (TA)s_s[k];
+                if (p < 0 || s_s[k] == (TA)0) continue;
+                const TA c = s_c[k], sn = s_s[k];
                 const TA ap = A[p * W + col], aq = A[q * W + col];
                 A[p * W + col] = c * ap - sn * aq;
                 A[q * W + col] = sn * ap + c * aq;
@@ -159,8 +193,8 @@ __device__ int jacobi_sweeps(TA *A, TQ *Q, int W, int max_sweeps, double eps) {
     return sweeps;
 }
 
-// Stage 1: FP32 Jacobi on S from Q = I (A and Q in shared memory); the
-// eigenvectors go to Qd in FP64.
+// Stage 1: FP32 Jacobi on S (or on Qp^T S Qp, warm start) from Q = I (A and
+// Q in shared memory); the eigenvectors go to Qd in FP64.
 __global__ void __launch_bounds__(kEigThreads) k_eig_f32(const double *S, int W, double *Qd, int *flags) {
     extern __shared__ __align__(16) float sm[];
     float *A = sm, *Q = sm + W * W;
@@ -169,38 +203,60 @@ __global__ void __launch_bounds__(kEigThreads) k_eig_f32(const double *S, int W,
         Q[e] = (e / W == e % W) ? 1.f : 0.f;
     }
     __syncthreads();
-    const int sweeps = jacobi_sweeps<float, float>(A, Q, W, 40, 6e-8);
+    const int sweeps = jacobi_sweeps<float, float>(A, Q, W, 40, 6e-8, nullptr);
     for (int e = threadIdx.x; e < W * W; e += blockDim.x) Qd[e] = Q[e];
     if (threadIdx.x == 0) flags[1] = sweeps;
 }
 
-// C = op(A) B for W x W FP64 matrices (op: transpose when transA); one
-// thread per entry of C, spread over many CTAs (FP64 is slow per SM).
-__global__ void k_gemm64(const double *A, const double *B, double *C, int W, int transA) {
+// W x W FP64 products, one thread per entry of C, spread over many CTAs
+// (FP64 is slow per SM).  op 0: C = A B;  op 1: C = A^T B;  op 2: C =
+// A (1.5 I - 0.5 B), with B = A^T A: one Newton-Schulz (Lowdin) step that
+// makes the nearly orthonormal columns of A orthonormal to second order.
+__global__ void k_gemm64(const double *A, const double *B, double *C, int W, int op) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= W * W) return;
     const int i = e / W, j = e % W;
+    auto a = [&](int k) { return op == 1 ? A[k * W + i] : A[i * W + k]; };
+    auto b = [&](int k) { return op == 2 ? (k == j ? 1.5 : 0.0) - 0.5 * B[k * W + j] : B[k * W + j]; };
     double s0 = 0.0, s1 = 0.0;
     int k = 0;
     for (; k + 1 < W; k += 2) {
-        s0 = fma(transA ? A[k * W + i] : A[i * W + k], B[k * W + j], s0);
-        s1 = fma(transA ? A[(k + 1) * W + i] : A[i * W + k + 1], B[(k + 1) * W + j], s1);
+        s0 = fma(a(k), b(k), s0);
+        s1 = fma(a(k + 1), b(k + 1), s1);
     }
-    if (k < W) s0 = fma(transA ? A[k * W + i] : A[i * W + k], B[k * W + j], s0);
+    if (k < W) s0 = fma(a(k), b(k), s0);
     C[e] = s0 + s1;
 }
 
-// Stage 2: FP64 Jacobi on Aq = Q1^T S Q1 (nearly diagonal after stage 1),
-// accumulating into Qd = Q1 (global memory); then the R largest eigenvalues
+// Stage 2: FP64 Jacobi on Aq = Q1^T S Q1 (nearly diagonal after stage 1; Q1
+// re-orthonormalised in FP64 first, so that this is a similarity to FP64
+// rounding), accumulating into Qd = Q1 (global memory); then the R largest eigenvalues
 // (ties: lower index) and their 1 / sqrt(d).  A direction whose eigenvalue
 // is below 1e-12 of the largest counts as null (S is accurate to ~1e-13).
 __global__ void __launch_bounds__(kEigThreads) k_eig_refine(const double *Aq, int W, int R, double *Qd, int *sel,
                                                             double *dsel, double *inv_sig, int *flags) {
     extern __shared__ __align__(16) double smd[];
     double *A = smd;
+    __shared__ int act[kMaxW];
     for (int e = threadIdx.x; e < W * W; e += blockDim.x) A[e] = Aq[e];
     __syncthreads();
-    jacobi_sweeps<double, double>(A, Qd, W, 12, 1.1e-16);
+    // active set: the 2R + 2 largest diagonal entries (the FP32 stage has
+    // ordered the spectrum to ~1e-7 of its largest value)
+    if (threadIdx.x == 0) {
+        const int K = min(W, 2 * R + 2);
+        for (int c = 0; c < W; ++c) act[c] = 0;
+        for (int r = 0; r < K; ++r) {
+            int best = -1;
+            for (int c = 0; c < W; ++c)
+                if (!act[c] && (best < 0 || A[c * W + c] > A[best * W + best])) best = c;
+            act[best] = 1;
+        }
+    }
+    __syncthreads();
+    // from the FP32 stage's off-diagonal level (~1e-7 of the largest entry)
+    // the rotations against the active indices converge quadratically: three
+    // sweeps reach FP64 rounding
+    jacobi_sweeps<double, double>(A, Qd, W, 3, 1.1e-16, act);
     __syncthreads();
     if (threadIdx.x == 0) {
         double dmax = 0.0;
@@ -290,12 +346,13 @@ __global__ void __launch_bounds__(kProjWarps * 32) k_project(const float *Y, int
     }
 }
 
-// sign_r = sign of column r's entry of largest magnitude (first row on ties)
-__global__ void k_sign(const float *cand, int nb, int R, float *sgn) {
-    const int r = threadIdx.x;
-    if (r >= R) return;
+// sign_r = sign of column r's entry of largest magnitude (first row on
+// ties); one CTA per column, the per-CTA candidates reduced in parallel.
+__global__ void __launch_bounds__(256) k_sign(const float *cand, int nb, int R, float *sgn) {
+    __shared__ float s_m[256], s_i[256], s_v[256];
+    const int r = blockIdx.x;
     float m = -1.f, ix = 0.f, v = 0.f;
-    for (int b = 0; b < nb; ++b) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         const float *cb = cand + ((int64_t)b * R + r) * 3;
         if (cb[0] > m || (cb[0] == m && cb[0] >= 0.f && cb[1] < ix)) {
             m = cb[0];
@@ -303,7 +360,23 @@ __global__ void k_sign(const float *cand, int nb, int R, float *sgn) {
             v = cb[2];
         }
     }
-    sgn[r] = v < 0.f ? -1.f : 1.f;
+    s_m[threadIdx.x] = m;
+    s_i[threadIdx.x] = ix;
+    s_v[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            const float m2 = s_m[threadIdx.x + o], i2 = s_i[threadIdx.x + o];
+            const float m1 = s_m[threadIdx.x], i1 = s_i[threadIdx.x];
+            if (m2 > m1 || (m2 == m1 && m2 >= 0.f && i2 < i1)) {
+                s_m[threadIdx.x] = m2;
+                s_i[threadIdx.x] = i2;
+                s_v[threadIdx.x] = s_v[threadIdx.x + o];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sgn[r] = s_v[0] < 0.f ? -1.f : 1.f;
 }
 
 __global__ void k_flip(float *U, int64_t n, int R, const float *sgn) {
@@ -367,6 +440,7 @@ extern "C" int tucker_state_create(int nmodes, const uint32_t *dims, int R, cons
     for (int k = 0; k < nmodes; ++k) oU[k] = take((size_t)dims[k] * R * 4);
     const size_t oY = take((size_t)st->max_dim * W * 4), oS = take((size_t)W * W * 8), oQ = take((size_t)W * W * 8),
                  oT1 = take((size_t)W * W * 8), oAq = take((size_t)W * W * 8), oDs = take((size_t)R * 8),
+                 oQp = take((size_t)nmodes * W * W * 8),
                  oP = take((size_t)std::max<int64_t>(nbg * W * W, 1024) * 8), oC = take((size_t)nbp * R * 3 * 4),
                  oSel = take((size_t)R * 4), oIs = take((size_t)R * 8), oSg = take((size_t)R * 4),
                  oSc = take(4 * 8), oF = take(2 * 4);
@@ -383,6 +457,7 @@ extern "C" int tucker_state_create(int nmodes, const uint32_t *dims, int R, cons
     st->T1 = reinterpret_cast<double *>(b + oT1);
     st->Aq = reinterpret_cast<double *>(b + oAq);
     st->dsel = reinterpret_cast<double *>(b + oDs);
+    for (int k = 0; k < nmodes; ++k) st->Qprev[k] = reinterpret_cast<double *>(b + oQp) + (size_t)k * W * W;
     st->part = reinterpret_cast<double *>(b + oP);
     st->cand = reinterpret_cast<float *>(b + oC);
     st->sel = reinterpret_cast<int *>(b + oSel);
@@ -452,17 +527,33 @@ extern "C" int tucker_hooi_iter(const fcoo_t *const *Xn, tucker_state_t *st, fco
         if (rc) return rc;
         rc = gram_f32_fp64(st->Y, I, W, st->part, st->S, s);
         if (rc) return rc;
-        // eigenvectors of S: FP32 Jacobi, then FP64 sweeps on Q1^T S Q1
-        k_eig_f32<<<1, kEigThreads, eig_smem, s>>>(st->S, W, st->Qd, st->flags);
+        // eigenvectors of S: FP32 Jacobi (on Qp^T S Qp from the mode's last
+        // eigenvectors Qp once there are some: nearly diagonal after the first
+        // iteration, so few sweeps); Q1 re-orthonormalised in FP64 (Q1 <- Q1
+        // (1.5 I - 0.5 Q1^T Q1)); FP64 sweeps on Q1^T S Q1
+        if (st->have_q[n]) {
+            k_gemm64<<<gg, 128, 0, s>>>(st->S, st->Qprev[n], st->T1, W, 0);
+            k_gemm64<<<gg, 128, 0, s>>>(st->Qprev[n], st->T1, st->Aq, W, 1);
+            k_eig_f32<<<1, kEigThreads, eig_smem, s>>>(st->Aq, W, st->Qd, st->flags);
+            k_gemm64<<<gg, 128, 0, s>>>(st->Qprev[n], st->Qd, st->T1, W, 0);
+            std::swap(st->Qd, st->T1);
+        } else {
+            k_eig_f32<<<1, kEigThreads, eig_smem, s>>>(st->S, W, st->Qd, st->flags);
+        }
+        k_gemm64<<<gg, 128, 0, s>>>(st->Qd, st->Qd, st->Aq, W, 1);
+        k_gemm64<<<gg, 128, 0, s>>>(st->Qd, st->Aq, st->T1, W, 2);
+        std::swap(st->Qd, st->T1);
         k_gemm64<<<gg, 128, 0, s>>>(st->S, st->Qd, st->T1, W, 0);
         k_gemm64<<<gg, 128, 0, s>>>(st->Qd, st->T1, st->Aq, W, 1);
         k_eig_refine<<<1, kEigThreads, ref_smem, s>>>(st->Aq, W, R, st->Qd, st->sel, st->dsel, st->inv_sig,
                                                        st->flags);
         FCOO_CUDA(cudaGetLastError());
+        FCOO_CUDA(cudaMemcpyAsync(st->Qprev[n], st->Qd, (size_t)W * W * 8, cudaMemcpyDeviceToDevice, s));
+        st->have_q[n] = true;
         const int nb = proj_blocks(I);
         k_project<<<nb, kProjWarps * 32, 0, s>>>(st->Y, I, W, st->Qd, st->sel, st->inv_sig, R, st->U[n], st->cand);
         FCOO_CUDA(cudaGetLastError());
-        k_sign<<<1, 32, 0, s>>>(st->cand, nb, R, st->sgn);
+        k_sign<<<R, 256, 0, s>>>(st->cand, nb, R, st->sgn);
         const int64_t ne = I * R;
         k_flip<<<(unsigned)std::min<int64_t>(ceil_div(ne, 256), 4096), 256, 0, s>>>(st->U[n], ne, R, st->sgn);
         FCOO_CUDA(cudaGetLastError());
