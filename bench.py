@@ -444,6 +444,11 @@ def bench_sweep(fc, dev, quick):
     return out
 
 
+def ttm_handle(fc, T, dims, mode):
+    """The SpTTM handle along `mode` of the workload tensor T (on the device)."""
+    return fc.FCOO.build([a.to(torch.int32).contiguous() for a in T.idx], T.val, dims, mode, "ttm", 8)
+
+
 def bench_mttkrp_bf16(fc, Xs, dims, R, steps=50):
     """The same three SpMTTKRP calls with BF16 factors (FP32 accumulation):
     half the gathered bytes per nonzero."""
@@ -457,21 +462,28 @@ def bench_mttkrp_bf16(fc, Xs, dims, R, steps=50):
             "per_mode_ms": [t * 1e3 for t in per_mode]}
 
 
-def bench_cp_als(fc, Xs, dims, sweeps, R=64, fp32_tail=2):
+def bench_cp_als(fc, Xs, dims, sweeps, R=64, fp32_tail=2, Xttm=None):
     """CP-ALS, R = 64, `sweeps` sweeps from the same U(0,1) start: FP32 factor
     storage; BF16 storage throughout; and the mixed schedule, BF16 storage for
     all but the last `fp32_tail` sweeps, which run on FP32 storage
-    (cp_state_set_dtype).  Seconds per sweep over sweeps 2..`sweeps` (the
-    first sweep, which also takes |X|^2, is outside the timing)."""
+    (cp_state_set_dtype).  With Xttm (the SpTTM handle along mode 2), the
+    same three again with modes 0 and 1 through the mode-2 fibre sums
+    ("*_fibres").  Seconds per sweep over sweeps 2..`sweeps` (the first
+    sweep, which also takes |X|^2, is outside the timing)."""
     init = synth.make_factors(dims, R, seed=0, kind="uniform")
     res = {}
-    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16), ("mixed", torch.bfloat16)):
+    variants = [("fp32", torch.float32), ("bf16", torch.bfloat16), ("mixed", torch.bfloat16)]
+    if Xttm is not None:
+        variants += [(n + "_fibres", dt) for n, dt in variants]
+    for name, dt in variants:
         st = fc.CPState(dims, R, init, dtype=dt)
+        if name.endswith("_fibres"):
+            st.use_fibres(Xttm)
         st.iterate(Xs)  # first sweep outside the timing (computes |X|^2 once)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        if name == "mixed":
+        if name.startswith("mixed"):
             st.iterate(Xs, sweeps=sweeps - 1 - fp32_tail)
             st.set_dtype(torch.float32)
             st.iterate(Xs, sweeps=fp32_tail)
@@ -485,9 +497,10 @@ def bench_cp_als(fc, Xs, dims, sweeps, R=64, fp32_tail=2):
         st.close()
     out = {"R": R, "sweeps": sweeps, "mixed_schedule": f"BF16 storage for sweeps 1-{sweeps - fp32_tail}, "
                                                         f"FP32 for the last {fp32_tail}"}
-    for name in ("fp32", "bf16", "mixed"):
+    names = [n for n, _ in variants]
+    for name in names:
         out[name] = {k: v for k, v in res[name].items() if k != "factors"}
-    for name in ("bf16", "mixed"):
+    for name in names[1:]:
         out[name]["fit_diff_vs_fp32"] = abs(res[name]["fit"] - res["fp32"]["fit"])
         out[name]["factor_rel_vs_fp32"] = [
             float(torch.linalg.norm(res[name]["factors"][k] - res["fp32"]["factors"][k]) /
@@ -611,7 +624,8 @@ def run_ours(args):
                          ("spttm", lambda: bench_spttm(fc, dev, args.quick)),
                          ("spttmc", lambda: bench_spttmc(fc, Xs, cfg.dims, dev, T)),
                          ("tucker", lambda: bench_tucker(fc, Xs, cfg.dims)),
-                         ("cp_als", lambda: bench_cp_als(fc, Xs, cfg.dims, 20 if not args.quick else 5)),
+                         ("cp_als", lambda: bench_cp_als(fc, Xs, cfg.dims, 20 if not args.quick else 5,
+                                                         Xttm=ttm_handle(fc, T, cfg.dims, 2))),
                          ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick))):
             try:
                 line[name] = fn()
@@ -700,8 +714,8 @@ def main():
             line["tucker"] = bench_tucker(fc, Xs, cfg.dims)
         else:
             cfg = workload_config(args)
-            _, Xs, _, _ = build_workload(cfg, dev)
-            line = bench_cp_als(fc, Xs, cfg.dims, args.sweeps)
+            T, Xs, _, _ = build_workload(cfg, dev)
+            line = bench_cp_als(fc, Xs, cfg.dims, args.sweeps, Xttm=ttm_handle(fc, T, cfg.dims, 2))
         print(json.dumps(line), flush=True)
         return
     if args.impl == "reference":

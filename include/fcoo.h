@@ -394,6 +394,26 @@ int cp_als_iter(const fcoo_t *const *Xn, cp_state_t *st, fcoo_stream_t stream);
  * the number of completed sweeps and the number of pseudo-inverse solves. */
 int cp_state_stats(const cp_state_t *st, double *lambda, double *fit, int *iters, int *npinv, fcoo_stream_t stream);
 
+/* Fibre reuse for 3-way CP-ALS.  SpMTTKRP of modes 0 and 1 both contract
+ * the tensor with the mode-2 factor C, which does not change between their
+ * updates.  With this on, mode 0 first forms the mode-2 fibre sums
+ *   T(f, :) = sum_k X(i,j,k) C(k, :)      for each fibre f = (i, j)   (Eq. 3)
+ * and modes 0 and 1 each run Eq. 6 over the fibres, with factors (B, T) and
+ * (A, T), instead of over the nonzeros.  The result is the same up to
+ * rounding, and it pays where fibres hold several nonzeros.
+ *   Xttm       the SpTTM handle along mode 2 of the same tensor (op =
+ *              FCOO_OP_TTM, mode 2).  Not copied: it must outlive its use.
+ *              NULL turns the reuse off and frees its buffers.
+ *   threadlen  partition length of the fibre tensor's F-COO handles.
+ * The state holds two F-COO handles of nfib nonzeros, nfib x R FP32 fibre
+ * sums, and an FP32 copy of one factor (for BF16 storage).  Synchronous.
+ * Cost: the fibre sums are written once and read twice per sweep (nfib x R
+ * x 4 bytes each time).  On a 76M-nonzero Zipf tensor with 13M fibres at
+ * R = 64 that made FP32 sweeps 4 % faster and BF16 sweeps slower, so it is
+ * off unless asked for.
+ * Errors: FCOO_ERR_INVALID_ARG (not 3-way, wrong handle), FCOO_ERR_NOMEM. */
+int cp_state_use_fibres(cp_state_t *st, const fcoo_t *Xttm, int threadlen, fcoo_stream_t stream);
+
 /* Change the storage type of the factors (FCOO_F32 <-> FCOO_BF16) in place:
  * BF16 -> FP32 is exact; FP32 -> BF16 rounds to nearest even and recomputes
  * the Grams.  Later cp_als_iter sweeps gather the factors in the new type.

@@ -318,6 +318,14 @@ class CPState:
         except Exception:
             pass
 
+    def use_fibres(self, Xttm: Optional[FCOO], threadlen: int = 8, stream=None):
+        """3-way only: modes 0 and 1 reuse the mode-2 fibre sums (``Xttm`` is
+        the SpTTM handle along mode 2; None turns the reuse off)."""
+        check(lib.cp_state_use_fibres(self._h, Xttm.handle if Xttm is not None else None, int(threadlen),
+                                      _stream(stream)))
+        self._fib = Xttm  # keeps the handle alive
+        return self
+
     def iterate(self, Xn: Sequence[FCOO], sweeps: int = 1, stream=None):
         """Run ``sweeps`` sweeps of Algorithm 1 (asynchronous on the stream)."""
         hs = (ctypes.c_void_p * len(Xn))(*[x.handle.value for x in Xn])

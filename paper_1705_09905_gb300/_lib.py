@@ -90,6 +90,7 @@ SIGNATURES = {
     "cp_state_stats": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "cp_state_copy_factor": (_i, [_vp, _i, _vp, _vp]),
     "cp_state_set_dtype": (_i, [_vp, _i, _vp]),
+    "cp_state_use_fibres": (_i, [_vp, _vp, _i, _vp]),
     "cp_state_blob_size": (_i64, [_vp]),
     "cp_state_save": (_i, [_vp, _vp, _i64, _vp]),
     "cp_state_load": (_i, [_vp, _vp, _i64, _vp]),

@@ -19,7 +19,7 @@
 
 #include <algorithm>
 
-#include "internal.cuh"
+#include "fibre.cuh"
 
 struct cp_state {
     int nmodes, R, dtype;
@@ -43,6 +43,13 @@ struct cp_state {
     cudaEvent_t ev_fork, ev_join;
     void *base;
     size_t bytes;
+    // fibre reuse (3-way): modes 0 and 1 share the mode-2 fibre sums
+    // T(f, :) = sum_k X(i,j,k) C(k, :) (C does not change between their
+    // updates), each then an SpMTTKRP over the fibre tensor
+    const fcoo_t *fib_ttm;  // SpTTM handle along mode 2 (not owned)
+    fcoo_t *fib_X[2];       // fibre tensor, SpMTTKRP handles for modes 0 and 1
+    float *fib_T;           // nfib x R
+    float *fib_f32;         // FP32 copy of a BF16 factor (max(I_0, I_1) x R)
 };
 
 namespace fcx {
@@ -665,6 +672,64 @@ int gram_of(cp_state_t *st, int k, cudaStream_t s) {
     return FCOO_OK;
 }
 
+__global__ void k_bf16_to_f32(const __nv_bfloat16 *a, int64_t n, float *b) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = __bfloat162float(a[e]);
+}
+
+void fibres_release(cp_state_t *st) {
+    for (int k = 0; k < 2; ++k) {
+        if (st->fib_X[k]) fcoo_destroy(st->fib_X[k]);
+        st->fib_X[k] = nullptr;
+    }
+    dev_free(st->fib_T);
+    dev_free(st->fib_f32);
+    st->fib_T = st->fib_f32 = nullptr;
+    st->fib_ttm = nullptr;
+}
+
+// M = SpMTTKRP of mode n < 2 through the fibre sums: for mode 0 first the
+// sums T = SpTTM along mode 2 with the current C (Eq. 3), then Eq. 6 over the
+// fibre tensor with factors (B, T) for mode 0 or (A, T) for mode 1, in FP32
+// (a BF16 factor is widened first).  Both launches leave one CTA slot for
+// the solve on the side stream.
+int mode_mttkrp_fibres(cp_state_t *st, int n, cudaStream_t s) {
+    const int R = st->R;
+    if (n == 0 && st->fib_ttm->nnz > 0) {
+        StreamParams q;
+        stream_params_from(st->fib_ttm, q);
+        q.F[0] = st->F[2];
+        q.out = st->fib_T;
+        q.R = R;
+        q.out_rows = st->fib_ttm->nseg;
+        q.reserve_ctas = 1;
+        int rc = launch_stream_kernel(q, st->dtype, s);
+        if (rc) return rc;
+    }
+    const fcoo_t *Xf = st->fib_X[n];
+    if (Xf->nnz == 0) {
+        FCOO_CUDA(cudaMemsetAsync(st->M, 0, (size_t)st->dims[n] * R * 4, s));
+        return FCOO_OK;
+    }
+    const void *other = st->F[1 - n];
+    if (st->dtype == FCOO_BF16) {
+        const int64_t ne = (int64_t)st->dims[1 - n] * R;
+        k_bf16_to_f32<<<(unsigned)std::min<int64_t>(ceil_div(ne, 256), 4096), 256, 0, s>>>(
+            (const __nv_bfloat16 *)other, ne, st->fib_f32);
+        FCOO_CUDA(cudaGetLastError());
+        other = st->fib_f32;
+    }
+    StreamParams p;
+    stream_params_from(Xf, p);
+    p.F[0] = other;      // product modes of the fibre tensor: the other index mode, then f
+    p.F[1] = st->fib_T;
+    p.out = st->M;
+    p.R = R;
+    p.out_rows = st->dims[n];
+    p.reserve_ctas = 1;
+    return launch_stream_kernel(p, FCOO_F32, s);
+}
+
 // One mode update of Algorithm 1.
 int mode_update(const fcoo_t *X, cp_state_t *st, int n, bool last, cudaStream_t s) {
     const int R = st->R;
@@ -694,7 +759,10 @@ int mode_update(const fcoo_t *X, cp_state_t *st, int n, bool last, cudaStream_t 
     p.R = R;
     p.out_rows = I;
     p.reserve_ctas = 1;
-    if (X->nnz == 0) {
+    if (st->fib_ttm && n < 2) {
+        int rc = mode_mttkrp_fibres(st, n, s);
+        if (rc) return rc;
+    } else if (X->nnz == 0) {
         FCOO_CUDA(cudaMemsetAsync(st->M, 0, (size_t)I * R * 4, s));
     } else {
         int rc = launch_stream_kernel(p, st->dtype, s);
@@ -882,8 +950,37 @@ extern "C" int cp_state_destroy(cp_state_t *st) {
     if (st->ev_join) cudaEventDestroy(st->ev_join);
     if (st->ev_fork) cudaEventDestroy(st->ev_fork);
     if (st->side) cudaStreamDestroy(st->side);
+    fibres_release(st);
     dev_free(st->base);
     free(st);
+    return FCOO_OK;
+}
+
+extern "C" int cp_state_use_fibres(cp_state_t *st, const fcoo_t *Xttm, int threadlen, fcoo_stream_t stream) {
+    clear_error();
+    if (!st) return fail(FCOO_ERR_INVALID_ARG, "cp_state_use_fibres: NULL state");
+    cudaStream_t s = (cudaStream_t)stream;
+    FCOO_CUDA(cudaStreamSynchronize(s));
+    fibres_release(st);
+    if (!Xttm) return FCOO_OK;
+    if (st->nmodes != 3 || Xttm->op != FCOO_OP_TTM || Xttm->nmodes != 3 || Xttm->mode != 2)
+        return fail(FCOO_ERR_INVALID_ARG, "cp_state_use_fibres: needs a 3-way state and the SpTTM handle along mode 2");
+    for (int k = 0; k < 3; ++k)
+        if (Xttm->dims[k] != st->dims[k]) return fail(FCOO_ERR_INVALID_ARG, "cp_state_use_fibres: dims differ");
+    int rc = FCOO_OK;
+    for (int k = 0; k < 2 && rc == FCOO_OK; ++k) rc = fibre_tensor_build(Xttm, k, threadlen, s, &st->fib_X[k]);
+    if (rc == FCOO_OK) {
+        cudaError_t e = dev_alloc(reinterpret_cast<void **>(&st->fib_T), (size_t)std::max<int64_t>(Xttm->nseg, 1) * st->R * 4);
+        if (e == cudaSuccess)
+            e = dev_alloc(reinterpret_cast<void **>(&st->fib_f32),
+                          (size_t)std::max(st->dims[0], st->dims[1]) * st->R * 4);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cp_state_use_fibres");
+    }
+    if (rc != FCOO_OK) {
+        fibres_release(st);
+        return rc;
+    }
+    st->fib_ttm = Xttm;
     return FCOO_OK;
 }
 
@@ -899,6 +996,8 @@ extern "C" int cp_als_iter(const fcoo_t *const *Xn, cp_state_t *st, fcoo_stream_
             if (X->dims[k] != st->dims[k]) return fail(FCOO_ERR_INVALID_ARG, "cp_als_iter: Xn[%d] dims differ", n);
         if (X->nnz != Xn[0]->nnz) return fail(FCOO_ERR_INVALID_ARG, "cp_als_iter: handles hold different tensors");
     }
+    if (st->fib_ttm && st->fib_ttm->nnz != Xn[0]->nnz)
+        return fail(FCOO_ERR_INVALID_ARG, "cp_als_iter: the fibre handle holds a different tensor");
     cudaStream_t s = (cudaStream_t)stream;
     const int R = st->R;
     if (!st->have_norm) {

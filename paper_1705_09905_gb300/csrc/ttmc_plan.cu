@@ -8,7 +8,7 @@
 // and then
 //   Y(i, r_a * R + r_b) = sum_{fibres f of slice i} U_a(j_f, r_a) T(f, r_b),
 // which is Eq. 4 again, on the 3-way "fibre tensor" X'(i, j_f, f) = 1 with
-// factors U_a and T.  A nonzero then costs R FMAs (plus R^2 per fibre)
+// factors U_a and T (fibre.cu).  A nonzero then costs R FMAs (plus R^2 per fibre)
 // instead of R^2: fewer operations wherever fibres hold more than one
 // nonzero.  Both passes are the streaming kernel: SpTTM (kind 0, one
 // product mode) into T, then the Kronecker-column kind over X'.
@@ -17,34 +17,16 @@
 #include <algorithm>
 #include <new>
 
-#include "internal.cuh"
+#include "fibre.cuh"
 
 struct fcoo_ttmc_plan {
     const fcoo_t *Xttm;  // SpTTM handle along mode b (not owned)
-    fcoo_t *Xf;          // the fibre tensor X'(i, j_f, f), an SpMTTKRP handle on mode 0
+    fcoo_t *Xf;          // the fibre tensor X'(k0, k1, f), an SpMTTKRP handle on mode `pos`
     int mode, a, b, R;
+    int pos;             // position of `mode` among the SpTTM handle's index modes
     int64_t nfib;
     float *T;  // nfib x R fibre sums
 };
-
-namespace fcx {
-namespace {
-
-// X' coordinates from the SpTTM handle's fibre tuples (nfib x 2, index
-// modes ascending): column cn is mode n, column ca is mode a; the third
-// coordinate is the fibre's own number; every value is 1.
-__global__ void k_fibre_coords(const uint32_t *keys, int64_t nfib, int cn, int ca, uint32_t *in, uint32_t *ia,
-                               uint32_t *iff, float *ones) {
-    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nfib; f += (int64_t)gridDim.x * blockDim.x) {
-        in[f] = keys[2 * f + cn];
-        ia[f] = keys[2 * f + ca];
-        iff[f] = (uint32_t)f;
-        ones[f] = 1.f;
-    }
-}
-
-}  // namespace
-}  // namespace fcx
 
 using namespace fcx;
 
@@ -74,35 +56,11 @@ extern "C" int spttmc_plan_create(const fcoo_t *Xttm, int mode, int R, int threa
     P->R = R;
     P->nfib = Xttm->nseg;
     const int64_t nf = P->nfib;
-    // the fibre tuples hold (index modes ascending) = the two modes other than b
-    const int cn = Xttm->idx_modes[0] == mode ? 0 : 1, ca = 1 - cn;
-    void *tmp = nullptr;
-    int st = FCOO_OK;
-    cudaError_t e = dev_alloc(&tmp, (size_t)(nf > 0 ? nf : 1) * 16);
-    if (e != cudaSuccess) {
-        delete P;
-        return cuda_fail(e, "spttmc_plan_create: scratch");
-    }
-    uint32_t *in = static_cast<uint32_t *>(tmp), *ia = in + nf, *iff = ia + nf;
-    float *ones = reinterpret_cast<float *>(iff + nf);
-    if (nf > 0) {
-        const int grid = (int)std::min<int64_t>(ceil_div(nf, 256), (int64_t)num_sms() * 8);
-        k_fibre_coords<<<grid, 256, 0, s>>>(Xttm->segkeys, nf, cn, ca, in, ia, iff, ones);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) st = cuda_fail(e, "k_fibre_coords");
-    }
-    if (st == FCOO_OK) {
-        const uint32_t dims[3] = {Xttm->dims[mode], Xttm->dims[a], (uint32_t)(nf > 0 ? nf : 1)};
-        const uint32_t *idx[3] = {in, ia, iff};
-        st = fcoo_build(3, dims, nf, idx, ones, 0, FCOO_OP_MTTKRP, threadlen, stream, &P->Xf);
-        if (st != FCOO_OK) {
-            // keep fcoo_build's message, prefixed with where it came from
-            char msg[400];
-            snprintf(msg, sizeof(msg), "%s", fcoo_last_error());
-            st = fail(st, "spttmc_plan_create: fibre tensor: %s", msg);
-        }
-    }
-    dev_free(tmp);
+    // the fibre tuples hold (index modes ascending) = mode and a: the fibre
+    // tensor's rows are the coordinate of `mode`
+    P->pos = Xttm->idx_modes[0] == mode ? 0 : 1;
+    int st = fibre_tensor_build(Xttm, P->pos, threadlen, s, &P->Xf);
+    cudaError_t e;
     if (st == FCOO_OK && nf > 0) {
         e = dev_alloc(reinterpret_cast<void **>(&P->T), (size_t)nf * R * 4);
         if (e != cudaSuccess) st = cuda_fail(e, "spttmc_plan_create: fibre sums");
@@ -134,7 +92,8 @@ extern "C" int spttmc_plan_run(const fcoo_ttmc_plan_t *P, const void *const *fac
     int st = spttm(P->Xttm, factors[P->b], FCOO_F32, R, P->T, stream);
     if (st != FCOO_OK) return st;
     // pass 2: Eq. 4 over the fibre tensor, factors U_a and the fibre sums
-    const void *f2[3] = {nullptr, factors[P->a], P->T};
+    const void *f2[3] = {nullptr, nullptr, P->T};
+    f2[1 - P->pos] = factors[P->a];
     return spttmc(P->Xf, f2, FCOO_F32, R, out, stream);
 }
 

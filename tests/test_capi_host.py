@@ -93,6 +93,7 @@ def test_compute_entry_points_reject_null_handles(fc):
     assert lib.spttmc_plan_run(None, None, 0, None, None) == -1
     assert lib.spttmc_plan_info(None, None, None) == -1
     assert lib.tucker_hooi_iter(None, None, None) == -1
+    assert lib.cp_state_use_fibres(None, None, 8, None) == -1
     assert lib.tucker_state_stats(None, None, None, None, None, None) == -1
     assert lib.tucker_state_copy_factor(None, 0, None, None) == -1
     assert b"NULL" in lib.fcoo_last_error()

@@ -1,7 +1,8 @@
 """CP-ALS (Algorithm 1) on the device vs the FP64 oracle: factors, lambda and
 fit per sweep (FP32), the BF16 path against the oracle fed the same rounded
-factors step by step, the pseudo-inverse fallback, monotone fit, exact
-recovery of a low-rank tensor, checkpoint / resume."""
+factors step by step, the fibre reuse of modes 0 and 1 (FP32 and BF16), the
+pseudo-inverse fallback, monotone fit, exact recovery of a low-rank tensor,
+checkpoint / resume."""
 import numpy as np
 import pytest
 import torch
@@ -108,6 +109,84 @@ def test_mixed_schedule_switches_storage(fc, oracle):
         assert torch.equal(st.factor(k).cpu(), f32[k].to(torch.bfloat16).float())
     st.iterate(Xs)
     assert np.isfinite(st.stats()["fit"])
+
+
+def skewed_small():
+    # Zipf indices: fibres hold several nonzeros, as on the full workload
+    return synth.make_tensor(synth.scaled(synth.CONFIGS["skewed3"], 200_003, dims=(300, 250, 700)))
+
+
+@pytest.mark.parametrize("R", [8, 16])
+def test_fibre_reuse_fp32_matches_oracle(fc, oracle, R):
+    """Modes 0 and 1 through the mode-2 fibre sums (cp_state_use_fibres).
+    Each mode update of each sweep is checked on its own against the oracle's
+    update from the factors the device held when it made it (the Zipf
+    tensor's normal matrices are ill-conditioned, so errors compounded over
+    sweeps say nothing about one update).  The bound is FP32 rounding times
+    cond(V), at least 1e-4.  The fit is checked against the oracle and the
+    direct path on the device."""
+    T = skewed_small()
+    Xs = handles(fc, T)
+    Xt = fc.FCOO.build(T.idx_u32(), T.val.numpy(), T.dims, 2, "ttm", 8)
+    assert Xt.nseg < 0.7 * T.nnz
+    init = synth.make_factors(T.dims, R, seed=3, kind="uniform")
+    st = fc.CPState(T.dims, R, init).use_fibres(Xt)
+    direct = fc.CPState(T.dims, R, init)
+    idx, val = T.idx_u32(), T.val.double().numpy()
+    for sweep in range(3):
+        before = [st.factor(k).cpu().double().numpy() for k in range(3)]
+        st.iterate(Xs)
+        direct.iterate(Xs)
+        after = [st.factor(k).cpu().double().numpy() for k in range(3)]
+        for n in range(3):
+            inputs = [after[k] if k < n else before[k] for k in range(3)]
+            V = np.ones((R, R))
+            for k in range(3):
+                if k != n:
+                    V *= inputs[k].T @ inputs[k]
+            tol = max(1e-4, 5e-8 * np.linalg.cond(V))
+            Fo, lam, _, _ = oracle.cp_als_mode(T.dims, idx, val, inputs, n)
+            assert rel_fro(after[n], Fo[n]) <= tol, (sweep, n, rel_fro(after[n], Fo[n]), tol)
+        s, d = st.stats(), direct.stats()
+        assert abs(s["fit"] - oracle.cp_fit(T.dims, idx, val, after, s["lambda"])) <= 1e-5, sweep
+        assert abs(s["fit"] - d["fit"]) <= 1e-6, sweep
+
+
+def test_fibre_reuse_bf16_and_off(fc, oracle):
+    """BF16 storage through the fibre sums (the BF16 factor widened to FP32,
+    the fibre sums gathered from BF16 C): each mode update against the
+    oracle's update from the device's (BF16) factors of that moment, rounded
+    to BF16 like the device's; then the reuse turned off mid-run continues on
+    the direct path."""
+    T = skewed_small()
+    Xs = handles(fc, T)
+    Xt = fc.FCOO.build(T.idx_u32(), T.val.numpy(), T.dims, 2, "ttm", 8)
+    R = 16
+    init = synth.make_factors(T.dims, R, seed=4, kind="uniform")
+    st = fc.CPState(T.dims, R, init, dtype=torch.bfloat16).use_fibres(Xt)
+    idx, val = T.idx_u32(), T.val.double().numpy()
+    rnd = lambda a: torch.as_tensor(a).to(torch.bfloat16).double().numpy()
+    for sweep in range(2):
+        before = [st.factor(k).cpu().double().numpy() for k in range(3)]
+        st.iterate(Xs)
+        after = [st.factor(k).cpu().double().numpy() for k in range(3)]
+        for n in range(3):
+            inputs = [after[k] if k < n else before[k] for k in range(3)]
+            V = np.ones((R, R))
+            for k in range(3):
+                if k != n:
+                    V *= inputs[k].T @ inputs[k]
+            # a few entries may round to the neighbouring BF16 value
+            tol = max(2e-3, 5e-8 * np.linalg.cond(V))
+            Fo, _, _, _ = oracle.cp_als_mode(T.dims, idx, val, inputs, n)
+            assert rel_fro(after[n], rnd(Fo[n])) <= tol, (sweep, n, rel_fro(after[n], rnd(Fo[n])), tol)
+        s = st.stats()
+        assert abs(s["fit"] - oracle.cp_fit(T.dims, idx, val, after, s["lambda"])) <= 1e-4, sweep
+    st.use_fibres(None)
+    st.iterate(Xs)
+    assert np.isfinite(st.stats()["fit"])
+    with pytest.raises(fc.FcooError):
+        st.use_fibres(fc.FCOO.build(T.idx_u32(), T.val.numpy(), T.dims, 1, "ttm", 8))
 
 
 @pytest.mark.parametrize("R", [112, 120])
