@@ -5,8 +5,11 @@
 //   Y   = SpTTMc_n(X; U_k, k != n)            I_n x W, W = R^(N-1)   (k_stream kind 2)
 //   S   = Y^T Y                               W x W, Dot2 partials summed in FP64
 //   S   = Q diag(d) Q^T                        parallel cyclic Jacobi: FP32 sweeps
-//                                              from Q = I, then FP64 sweeps on
-//                                              Q^T S Q (one CTA each)
+//                                              (from the mode's last eigenvectors
+//                                              once there are some), an FP64
+//                                              re-orthonormalisation, then FP64
+//                                              sweeps on Q^T S Q against the
+//                                              2R + 2 leading directions
 //   U_n = Y q_r / sqrt(d_r) for the R largest d_r (FP64 sums): the R leading
 //         left singular vectors of Y_(n); each column signed so that its
 //         largest entry is positive
@@ -38,7 +41,7 @@ struct tucker_state {
     double *dsel;              // R selected eigenvalues
     float *sgn;                // R column signs
     double *scal;              // [0] |X|^2, [1] fit, [2] |G|^2
-    int *flags;                // [0] null directions met, [1] Jacobi sweeps of the last solve
+    int *flags;                // [0] null directions met, [1] FP32 Jacobi sweeps of the last solve
     int iters;
     bool have_norm;
     void *base;
