@@ -128,13 +128,20 @@ __device__ int jacobi_sweeps(TA *A, TQ *Q, int W, int max_sweeps, double eps, co
                 if (q < W && (!act || act[p] || act[q])) {
                     const TA apq = A[p * W + q];
                     if (apq != (TA)0) {
-                        const TA theta = (A[q * W + q] - A[p * W + p]) / (2 * apq);
-                        const TA at = theta >= 0 ? theta : -theta;
-                        // t = tan of the rotation angle (the smaller root)
-                        const TA t = at > (TA)1e15 ? (TA)0.5 / theta
-                                                   : (theta >= 0 ? (TA)1 : (TA)-1) / (at + sqrt(theta * theta + 1));
-                        c = 1 / sqrt(t * t + 1);
-                        sn = t * c;
+                        // t = tan of the rotation angle (the smaller root), in
+                        // FP32: a rotation then leaves ~1e-7 of a_pq, which
+                        // FP64 sweeps started at FP32 level absorb in two
+                        const float theta = (float)(A[q * W + q] - A[p * W + p]) / (float)(2 * apq);
+                        const float at = fabsf(theta);
+                        const float tf = at > 1e15f ? 0.5f / theta
+                                                    : (theta >= 0.f ? 1.f : -1.f) / (at + sqrtf(theta * theta + 1.f));
+                        const TA t = (TA)tf, u = t * t + 1;
+                        // c = 1/sqrt(u) exactly enough that c^2 + s^2 = 1 in TA:
+                        // the FP32 estimate plus one Newton step
+                        TA cc = (TA)rsqrtf((float)u);
+                        if (sizeof(TA) > 4) cc = cc * ((TA)1.5 - (TA)0.5 * u * cc * cc);
+                        c = cc;
+                        sn = t * cc;
                         rot = true;
                     }
                 }
