@@ -74,8 +74,12 @@ CONFIGS = {
 
 def scaled(cfg: TensorConfig, nnz: int, dims: Optional[Sequence[int]] = None, **kw) -> TensorConfig:
     """Same recipe with fewer nonzeros (and optionally smaller dims)."""
-    return replace(cfg, nnz=int(nnz), dims=tuple(dims) if dims is not None else cfg.dims,
-                   name=f"{cfg.name}@{nnz}", **kw)
+    d = tuple(dims) if dims is not None else cfg.dims
+    if int(nnz) == cfg.nnz and d == cfg.dims:
+        note = cfg.note
+    else:
+        note = f"{cfg.note}; scaled to {'x'.join(str(x) for x in d)}, {int(nnz)} nnz"
+    return replace(cfg, nnz=int(nnz), dims=d, name=f"{cfg.name}@{nnz}", note=note, **kw)
 
 
 def _gen(seed: int, device) -> torch.Generator:
