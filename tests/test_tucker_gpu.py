@@ -8,7 +8,8 @@ Inputs are sparse samples of a tensor of planted multilinear rank plus
 noise, so the R leading singular values are well separated and each factor
 column is unique up to the shared sign convention.  Also: the fit, the
 orthonormality of the factors, a fit that never decreases, exact recovery,
-4-way tensors (scalar SpTTMc lanes), rejected shapes, and the full skewed
+4-way tensors (scalar SpTTMc lanes), a matrix (two modes: the truncated SVD),
+rejected shapes, and the full skewed
 3-way tensor (76M nonzeros) against a numpy SVD of the device's SpTTMc."""
 import numpy as np
 import pytest
@@ -126,6 +127,26 @@ def test_hooi_exact_recovery(fc):
     st = fc.TuckerState(dims, R, start_factors(dims, R, seed=1))
     st.iterate(Xn, 2)
     assert st.stats()["fit"] > 0.999
+
+
+def test_hooi_2way_is_truncated_svd(fc):
+    """Two modes: HOOI alternates U0 <- lead(X U1), U1 <- lead(X^T U0), a
+    subspace iteration that converges to the R leading singular subspaces of
+    X; the fit then equals the truncated SVD's (numpy)."""
+    dims, R = (300, 200), 5
+    idx, val = planted(dims, R, 0.5, seed=21, noise=0.02)
+    Xn = build_all(fc, dims, idx, val)
+    st = fc.TuckerState(dims, R, start_factors(dims, R, seed=6))
+    st.iterate(Xn, 15)
+    X = np.zeros(dims)
+    X[idx[0], idx[1]] = val
+    U, sv, Vt = np.linalg.svd(X)
+    x2 = float(np.sum(val.astype(np.float64) ** 2))
+    fit_ref = 1 - np.sqrt(max(0.0, x2 - float(np.sum(sv[:R] ** 2)))) / np.sqrt(x2)
+    assert abs(st.stats()["fit"] - fit_ref) < 1e-5
+    P = U[:, :R] @ U[:, :R].T
+    U0 = st.factor(0).astype(np.float64)
+    np.testing.assert_allclose(U0 @ U0.T, P, atol=1e-4)
 
 
 def test_hooi_rejects(fc):
