@@ -99,3 +99,41 @@ def test_compute_entry_points_reject_null_handles(fc):
     assert b"NULL" in lib.fcoo_last_error()
     assert lib.spttmc_plan_destroy(None) == 0
     assert lib.fcoo_destroy(None) == 0
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/fcoo.h compiles as strict C99 and a C program links against
+    libfcoo.so and calls it (host-only entry points, and argument errors that
+    are returned before any device work): the boundary needs no C++ or torch."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "abi.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "fcoo.h"
+int main(void) {
+    if (fcoo_version() <= 0) return 1;
+    if (strcmp(fcoo_status_string(FCOO_ERR_INVALID_ARG), "") == 0) return 2;
+    if (fcoo_table2_bytes(2, 32 * 8, 8) != (4 + 8) * 256 + 256 / 8 + 256 / 64) return 3;
+    if (spmttkrp(NULL, NULL, FCOO_F32, 16, NULL, NULL) != FCOO_ERR_INVALID_ARG) return 4;
+    if (spttmc(NULL, NULL, FCOO_F32, 4, NULL, NULL) != FCOO_ERR_INVALID_ARG) return 5;
+    if (cp_als_iter(NULL, NULL, NULL) != FCOO_ERR_INVALID_ARG) return 6;
+    if (tucker_hooi_iter(NULL, NULL, NULL) != FCOO_ERR_INVALID_ARG) return 7;
+    if (strstr(fcoo_last_error(), "NULL") == NULL) return 8;
+    printf("ok\n");
+    return 0;
+}
+""")
+    libdir = os.path.join(ROOT, "paper_1705_09905_gb300", "lib")
+    exe = tmp_path / "abi"
+    cmd = [gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+           str(src), "-L", libdir, "-lfcoo", f"-Wl,-rpath,{libdir}", "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
