@@ -336,6 +336,7 @@ def bench_spttmc(fc, Xs, dims, dev, T=None):
         del idx32
     for R in (16, 8):
         F = [f.to(dev) for f in synth.make_factors(dims, R, seed=1)]
+        Fb = [f.to(torch.bfloat16) for f in F]
         row = {"R": R, "width": R * R, "modes": []}
         for n in range(3):
             Y = torch.empty((dims[n], R * R), device=dev)
@@ -344,6 +345,8 @@ def bench_spttmc(fc, Xs, dims, dev, T=None):
             byt = ttmc_alg_bytes(Xs[n], R)
             m = {"mode": n, "ms": t * 1e3, "TFLOPs": fl / t / 1e12, "frac_alu": fl / t / 1e12 / peak,
                  "GBps": byt / t / 1e9, "pct_hbm": byt / t / 1e9 / peaks()[0]}
+            tb = _time_calls(lambda: fc.spttmc(Xs[n], Fb, out=Y))
+            m["bf16_factors"] = {"ms": tb * 1e3, "TFLOPs": fl / tb / 1e12}
             if Xt:
                 plan = fc.SpTTMcPlan(Xt[1 if n == 2 else 2], n, R)
                 tp = _time_calls(lambda: plan.run(F, out=Y))

@@ -212,9 +212,9 @@ int spttm(const fcoo_t *X, const void *U, int dtype, int R, float *out, fcoo_str
  * Kronecker product U_{k_0}(j, :) (x) U_{k_1}(k, :) (x) ... (Eq. 1); the
  * first product mode varies slowest.
  * X        handle built with op = FCOO_OP_MTTKRP (the same handle SpMTTKRP uses)
- * factors  host array of N device pointers; factors[k] is dims[k] x R FP32
- *          row-major; factors[mode] is not read (may be NULL)
- * dtype    FCOO_F32 (FCOO_BF16 returns FCOO_ERR_UNSUPPORTED)
+ * factors  host array of N device pointers; factors[k] is dims[k] x R of
+ *          dtype, row-major; factors[mode] is not read (may be NULL)
+ * dtype    FCOO_F32 or FCOO_BF16 (BF16 storage, FP32 products and sums)
  * R        per-mode rank, R >= 1 with R^(N-1) <= FCOO_MAX_RANK
  *          (FCOO_ERR_UNSUPPORTED above)
  * out      device float32 dims[mode] x R^(N-1), row-major; every element is

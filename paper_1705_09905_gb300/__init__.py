@@ -196,13 +196,15 @@ def spttm(X: FCOO, U: torch.Tensor, out: Optional[torch.Tensor] = None, stream=N
 
 def spttmc(X: FCOO, factors: Sequence[Optional[torch.Tensor]], out: Optional[torch.Tensor] = None,
            stream=None) -> torch.Tensor:
-    """SpTTMc on the handle's mode (Eq. 4) with FP32 factors of one rank R:
-    dims[mode] x R^(N-1) float32, column ((r_a * R) + r_b) * R + ... over the
-    other modes a < b < ... (the first slowest).  Takes an SpMTTKRP handle."""
+    """SpTTMc on the handle's mode (Eq. 4) with factors of one rank R and one
+    dtype (float32 or bfloat16): dims[mode] x R^(N-1) float32, column
+    ((r_a * R) + r_b) * R + ... over the other modes a < b < ... (the first
+    slowest).  Takes an SpMTTKRP handle."""
     if X.op != MTTKRP:
         raise ValueError("SpTTMc takes a handle built for SpMTTKRP")
     ref = factors[X.prod_modes[0]]
     R = int(ref.shape[1])
+    dt = _dtype_code(ref)
     ptrs = []
     for k in range(X.nmodes):
         if k == X.mode:
@@ -210,13 +212,13 @@ def spttmc(X: FCOO, factors: Sequence[Optional[torch.Tensor]], out: Optional[tor
             continue
         f = factors[k]
         _check_factor(f, X.dims[k], R, f"factors[{k}]")
-        if f.dtype != torch.float32:
-            raise TypeError("SpTTMc takes float32 factors")
+        if f.dtype != ref.dtype:
+            raise TypeError("all factors must share one dtype")
         ptrs.append(f.data_ptr())
     if out is None:
         out = torch.empty((X.dims[X.mode], R ** (X.nmodes - 1)), dtype=torch.float32, device=ref.device)
     pp, _keep = ptr_array(ptrs)
-    check(lib.spttmc(X.handle, pp, F32, R, out.data_ptr(), _stream(stream)))
+    check(lib.spttmc(X.handle, pp, dt, R, out.data_ptr(), _stream(stream)))
     return out
 
 

@@ -123,7 +123,7 @@ void stream_params_from(const fcoo_t *X, StreamParams &p);
 
 // Launch the segmented-reduction kernel for dtype / R (spmttkrp.cu); kind 0
 // weights every nonzero by its value, kind 1 by the residual weight above,
-// kind 2 by its value with Kronecker output columns (SpTTMc, FP32 factors).
+// kind 2 by its value with Kronecker output columns (SpTTMc).
 int launch_stream_kernel(StreamParams &p, int dtype, cudaStream_t s, int kind = 0);
 // The instantiations, one translation unit each (stream_*.cu).
 int launch_stream_f32_k0(StreamParams &p, cudaStream_t s);
@@ -131,6 +131,7 @@ int launch_stream_f32_k1(StreamParams &p, cudaStream_t s);
 int launch_stream_bf16_k0(StreamParams &p, cudaStream_t s);
 int launch_stream_bf16_k1(StreamParams &p, cudaStream_t s);
 int launch_stream_f32_k2(StreamParams &p, cudaStream_t s);
+int launch_stream_bf16_k2(StreamParams &p, cudaStream_t s);
 
 // G = F^T F (R x R, FP64) of an I x R FP32 matrix: compensated (Dot2) FP32
 // partials over 128-row blocks (part: ceil(I/128) * R * R doubles), summed in

@@ -8,10 +8,7 @@
 namespace fcx {
 
 int launch_stream_kernel(StreamParams &p, int dtype, cudaStream_t s, int kind) {
-    if (kind == 2) {
-        if (dtype != FCOO_F32) return fail(FCOO_ERR_UNSUPPORTED, "SpTTMc takes FP32 factors only");
-        return launch_stream_f32_k2(p, s);
-    }
+    if (kind == 2) return dtype == FCOO_BF16 ? launch_stream_bf16_k2(p, s) : launch_stream_f32_k2(p, s);
     if (dtype == FCOO_BF16) return kind == 0 ? launch_stream_bf16_k0(p, s) : launch_stream_bf16_k1(p, s);
     return kind == 0 ? launch_stream_f32_k0(p, s) : launch_stream_f32_k1(p, s);
 }
@@ -76,7 +73,6 @@ extern "C" int spttmc(const fcoo_t *X, const void *const *factors, int dtype, in
     if (X->op != FCOO_OP_MTTKRP)
         return fail(FCOO_ERR_INVALID_ARG, "spttmc: the handle must be built with op = FCOO_OP_MTTKRP");
     if (dtype != FCOO_F32 && dtype != FCOO_BF16) return fail(FCOO_ERR_INVALID_ARG, "spttmc: dtype=%d unknown", dtype);
-    if (dtype != FCOO_F32) return fail(FCOO_ERR_UNSUPPORTED, "spttmc: FP32 factors only");
     if (R < 1) return fail(FCOO_ERR_INVALID_ARG, "spttmc: R=%d below 1", R);
     int64_t width = 1;
     for (int m = 0; m < X->nprod; ++m) {

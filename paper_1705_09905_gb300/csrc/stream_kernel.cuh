@@ -1138,8 +1138,8 @@ int launch_scalar(StreamParams &p, cudaStream_t s) {
 bool aligned(const void *q, uintptr_t a) { return q == nullptr || ((uintptr_t)q & (a - 1)) == 0; }
 
 // SpTTMc (kind 2): output width R = Rin^nprod.  3-way tensors with Rin = 8
-// or 16 (R = 64 or 256) take eight-column lanes, Rin = 4 (R = 16) four-column
-// lanes, each lane gathering one row piece per nonzero for all its chunks
+// or 16 (R = 64 or 256) take eight-column lanes (FP32 or BF16 rows), Rin = 4
+// (R = 16, FP32) four-column lanes, each lane gathering one row piece per nonzero for all its chunks
 // ((LPR / (Rin / E)) * NCH = Rin); every other shape the scalar lanes of the
 // general path.
 template <typename TF>
@@ -1157,7 +1157,8 @@ int launch_kron(StreamParams &p, cudaStream_t s) {
         if (p.Rin == 8) return launch_variant<TF, 8, 4, 2, 2, 2>(p, s);
         if (p.Rin == 16) return launch_variant<TF, 8, 16, 2, 2, 2>(p, s);
     }
-    if (p.nprod == 2 && p.Rin == 4 && all_aligned(16)) return launch_variant<TF, 4, 4, 1, 2, 2>(p, s);
+    if constexpr (std::is_same<TF, float>::value)  // four-column lanes: FP32 rows only
+        if (p.nprod == 2 && p.Rin == 4 && all_aligned(16)) return launch_variant<TF, 4, 4, 1, 2, 2>(p, s);
     const int nch = (p.R + 31) / 32;
     if (nch <= 1) return launch_variant<TF, 1, 32, 1, 0, 2>(p, s);
     if (nch <= 2) return launch_variant<TF, 1, 32, 2, 0, 2>(p, s);

@@ -2,7 +2,7 @@
 by element, on seeded inputs spanning several CTAs and ragged tails; every
 lane layout (eight-column lanes for 3-way R = 8 and 16, four-column lanes for
 R = 4, scalar lanes for the other ranks, for 2-way and 4-way tensors and for
-factors that are not 32-byte aligned), the edge cases (empty tensor, one hot
+factors that are not 32-byte aligned), BF16 factors, the edge cases (empty tensor, one hot
 slice, rejected shapes), determinism; the by-fibre plan (SpTTM into fibre
 sums, then Eq. 4 over the fibres) on every mode; and at the full skewed
 3-way size in the launch configuration bench.py times: every column
@@ -27,11 +27,11 @@ def fc():
     return fc
 
 
-def check_ttmc(fc, oracle, T, R, mode, tl=8, seed=1, factors=None):
+def check_ttmc(fc, oracle, T, R, mode, tl=8, seed=1, factors=None, dtype=torch.float32):
     dims = T.dims
     X = fc.FCOO.build(T.idx_u32(), T.val.numpy(), dims, mode, "mttkrp", tl)
     if factors is None:
-        factors = [f.to(cuda()) for f in synth.make_factors(dims, R, seed=seed)]
+        factors = [f.to(cuda()).to(dtype) for f in synth.make_factors(dims, R, seed=seed)]
     got = fc.spttmc(X, factors)
     torch.cuda.synchronize()
     Fh = host_factors(factors)
@@ -49,6 +49,13 @@ def test_tiny_config_vector_lanes(fc, oracle, R, mode):
     cfg = synth.CONFIGS["tiny"]
     T = synth.make_tensor(cfg)
     check_ttmc(fc, oracle, T, R, mode)
+
+
+@pytest.mark.parametrize("R,mode", [(8, 0), (16, 1), (16, 2), (5, 0), (3, 2)])
+def test_bf16_factors(fc, oracle, R, mode):
+    # the oracle gets the same BF16-rounded factor values upcast to FP64
+    T = synth.random_small((60, 50, 40), 8000, seed=40 + R)
+    check_ttmc(fc, oracle, T, R, mode, dtype=torch.bfloat16)
 
 
 @pytest.mark.parametrize("R", [1, 2, 3, 5, 10, 12, 15])
@@ -147,7 +154,6 @@ def test_rejected_shapes(fc):
     arr = (ctypes.c_void_p * 3)(*[f.data_ptr() for f in F])
     assert lib.spttmc(X.handle, arr, fc.F32, 17, out.data_ptr(), None) == -9  # R^2 > 256: unsupported
     assert b"above" in lib.fcoo_last_error()
-    assert lib.spttmc(X.handle, arr, fc.BF16, 4, out.data_ptr(), None) == -9
     assert lib.spttmc(Xt.handle, arr, fc.F32, 4, out.data_ptr(), None) == -1
     assert lib.spttmc(X.handle, arr, fc.F32, 0, out.data_ptr(), None) == -1
     assert lib.spttmc(X.handle, arr, fc.F32, 4, None, None) == -1
