@@ -75,6 +75,17 @@ int num_sms() {
     return n > 0 ? n : 1;
 }
 
+int device_sms(int dev) {
+    static std::atomic<int> cache[kMaxDevices];
+    if (dev < 0 || dev >= kMaxDevices) return num_sms();
+    int n = cache[dev].load(std::memory_order_acquire);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        cache[dev].store(n, std::memory_order_release);
+    }
+    return n;
+}
+
 void stream_params_from(const fcoo_t *X, StreamParams &p) {
     memset(&p, 0, sizeof(p));
     for (int m = 0; m < X->nprod; ++m) p.pidx[m] = X->pidx[m];

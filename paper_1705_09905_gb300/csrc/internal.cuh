@@ -33,6 +33,10 @@ void dev_free(void *p);
 void dev_free_async(void *p, cudaStream_t s);
 
 int num_sms();
+// SM count of device `dev`, looked up once per device (thread-safe).
+int device_sms(int dev);
+// Devices a process may use with per-device cached launch data.
+constexpr int kMaxDevices = 64;
 
 #define FCOO_CUDA(call)                                              \
     do {                                                             \

@@ -56,6 +56,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -951,6 +952,9 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         if (KIND == 1 && lig == 0) s_loss[g] = lsum;
     }
 
+    // lane groups of one warp leave their runs at different points: reconverge
+    // the warp before the CTA barrier
+    __syncwarp();
     __syncthreads();
     if (KIND == 1 && p.loss_part) {
         if (tid == 0) {
@@ -1062,31 +1066,40 @@ __global__ void __launch_bounds__(256) k_carry_fixup(const StreamParams p) {
 
 // ------------------------------------------------------------ launch
 
-int g_sms = 0;
-int sms() {
-    if (!g_sms) g_sms = num_sms();
-    return g_sms;
-}
-
 template <typename TF, int E, int LPR, int NCH, int NP, int KIND>
 int launch_variant(StreamParams &p, cudaStream_t s) {
     constexpr int G = kThreads / LPR;
     constexpr int RT = NCH * LPR * E;
     auto kern = k_stream<TF, E, LPR, NCH, NP, KIND>;
-    const size_t smem = stream_smem_bytes(p.nprod + 1 + (KIND == 1 ? 1 : 0), G, RT);
-    static size_t cached_smem = 0;
-    static int cached_occ = 0;
-    if (cached_smem != smem) {
-        FCOO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int occ = 0;
-        FCOO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
-        if (occ < 1) return fail(FCOO_ERR_UNSUPPORTED, "stream kernel does not fit on an SM (smem %zu)", smem);
-        cached_occ = occ;
-        cached_smem = smem;
+    // the shared memory size depends on the number of streams, which the
+    // general-N variant (NP = 0) takes at run time: one cache per size
+    const int nstream = p.nprod + 1 + (KIND == 1 ? 1 : 0);
+    const size_t smem = stream_smem_bytes(nstream, G, RT);
+    int dev = 0, occ = 0;
+    FCOO_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(FCOO_ERR_UNSUPPORTED, "device %d above %d", dev, kMaxDevices);
+    {
+        // per device: the largest shared-memory size the kernel was enabled
+        // for (only ever raised, so a launch never finds it lowered by
+        // another size), and its residency per stream count
+        static std::mutex mu;
+        static size_t attr_smem[kMaxDevices];
+        static int occ_plus1[kMaxDevices][FCOO_MAX_MODES + 2];
+        std::lock_guard<std::mutex> lock(mu);
+        if (smem > attr_smem[dev]) {
+            FCOO_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr_smem[dev] = smem;
+        }
+        if (!occ_plus1[dev][nstream]) {
+            FCOO_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+            if (occ < 1) return fail(FCOO_ERR_UNSUPPORTED, "stream kernel does not fit on an SM (smem %zu)", smem);
+            occ_plus1[dev][nstream] = occ + 1;
+        }
+        occ = occ_plus1[dev][nstream] - 1;
     }
     const int64_t ra = p.threadlen > 32 ? p.threadlen : 32;
     const int64_t max_ctas =
-        std::max<int64_t>(1, std::min<int64_t>((int64_t)sms() * cached_occ - p.reserve_ctas, p.grid));
+        std::max<int64_t>(1, std::min<int64_t>((int64_t)device_sms(dev) * occ - p.reserve_ctas, p.grid));
     int64_t grid = std::min<int64_t>(max_ctas, ceil_div(p.nnz, (int64_t)G * ra));
     if (grid < 1) grid = 1;
     p.run_len = round_up(ceil_div(p.nnz, grid * G), ra);
