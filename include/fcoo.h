@@ -304,9 +304,12 @@ int tucker_state_destroy(tucker_state_t *st);
 /* SpMTTKRP for callers that cannot allocate device memory                  */
 /* ---------------------------------------------------------------------- */
 
-/* Largest R and number of CTAs spmttkrp_noalloc accepts (they size its
- * fixed scratch: 2 * FCOO_NOALLOC_MAX_CTAS * FCOO_NOALLOC_MAX_RANK doubles
- * plus 2 * FCOO_NOALLOC_MAX_CTAS int64 = 2 MiB + 16 KiB). */
+/* The fixed scratch of spmttkrp_noalloc holds the carry slots of
+ * FCOO_NOALLOC_MAX_CTAS CTAs for ranks up to FCOO_NOALLOC_MAX_RANK:
+ * 2 * FCOO_NOALLOC_MAX_CTAS * FCOO_NOALLOC_MAX_RANK doubles plus
+ * 2 * FCOO_NOALLOC_MAX_CTAS int64 = 2 MiB + 16 KiB.  A larger R is refused;
+ * the CTA count is not a caller parameter: the launch uses at most
+ * FCOO_NOALLOC_MAX_CTAS CTAs. */
 #define FCOO_NOALLOC_MAX_RANK 128
 #define FCOO_NOALLOC_MAX_CTAS 1024
 
@@ -318,10 +321,15 @@ int tucker_state_destroy(tucker_state_t *st);
  *            for round_up(nnz, 32) entries (entries past nnz are read, unused)
  *   bf       ceil(nnz/32) words of segment-start bits; sf the start-flag words
  *            for partitions of `threadlen` nonzeros
- *   segrow   nseg output rows, one per segment, ascending
+ *   segrow   nseg output rows, one per segment, strictly ascending, each
+ *            below dims[mode]
  *   hcount   ceil(nnz/1024)+1 words: hcount[c] = number of set bits in
  *            bf[0 .. 32c-1] (segment starts before nonzero 1024c)
- * No pointer is retained after the call returns. */
+ * No pointer is retained after the call returns.  These buffers are trusted
+ * as they are: the call checks pointers, alignment and nseg <= dims[mode], but
+ * not the contents.  A layout that breaks the rules above (for example a
+ * segrow that is not strictly ascending or holds a row >= dims[mode]) makes
+ * the kernel read and write outside the buffers: behaviour is undefined. */
 typedef struct {
     int nmodes, mode, threadlen;
     int64_t nnz, nseg;
@@ -345,7 +353,8 @@ typedef struct {
  *               val(p) * prod_{k != mode} F_k(idx_k(p), :)
  *   factors  host array of nmodes device pointers, dims[k] x R of dtype
  *            (factors[mode] not read); R in 1..FCOO_NOALLOC_MAX_RANK
- *   out      device float32 dims[mode] x R, fully overwritten
+ *   out      device float32 dims[mode] x R, 4-byte aligned, fully
+ *            overwritten
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
  * scratch (2 MiB + 16 KiB) is a file-scope __device__ array held by every
  * GPU that loads the library until the process exits.  The first call on a
@@ -354,8 +363,10 @@ typedef struct {
  * capture.  Every call uses the same array, so calls that overlap on the GPU
  * (other streams, other threads) race and give wrong results: serialise them.
  * Nothing in the array has to start at zero: each launch initialises the
- * slots it reads.  Requests over the limits return FCOO_ERR_UNSUPPORTED with
- * a message.  Asynchronous on `stream`. */
+ * slots it reads.  R above FCOO_NOALLOC_MAX_RANK returns FCOO_ERR_UNSUPPORTED
+ * with a message; NULL or misaligned pointers and inconsistent sizes return
+ * FCOO_ERR_INVALID_ARG, both before any device work.  Asynchronous on
+ * `stream`. */
 int spmttkrp_noalloc(const fcoo_view_t *view, const void *const *factors, int dtype, int R, float *out,
                      fcoo_stream_t stream);
 

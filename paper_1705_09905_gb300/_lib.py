@@ -18,8 +18,11 @@ STATUS = {
     -4: "FCOO_ERR_NOMEM", -5: "FCOO_ERR_CUDA", -6: "FCOO_ERR_NOT_PD", -7: "FCOO_ERR_NONFINITE",
     -8: "FCOO_ERR_TIMEOUT", -9: "FCOO_ERR_UNSUPPORTED",
 }
+FCOO_ERR_INVALID_ARG = -1
+FCOO_ERR_UNSUPPORTED = -9
 MAX_MODES = 8
 MAX_RANK = 256
+NOALLOC_MAX_RANK = 128  # FCOO_NOALLOC_MAX_RANK
 
 
 class FcooError(RuntimeError):

@@ -53,11 +53,15 @@ extern "C" int spmttkrp_noalloc(const fcoo_view_t *v, const void *const *factors
                                 fcoo_stream_t stream) {
     clear_error();
     if (!v || !factors || !out) return fail(FCOO_ERR_INVALID_ARG, "spmttkrp_noalloc: NULL argument");
+    if (((uintptr_t)out & 3u) != 0) return fail(FCOO_ERR_INVALID_ARG, "spmttkrp_noalloc: out is not 4-byte aligned");
     if (v->nmodes < 2 || v->nmodes > FCOO_MAX_MODES || v->mode < 0 || v->mode >= v->nmodes)
         return fail(FCOO_ERR_INVALID_ARG, "spmttkrp_noalloc: bad nmodes/mode");
     if (!pow2_threadlen(v->threadlen)) return fail(FCOO_ERR_INVALID_ARG, "spmttkrp_noalloc: bad threadlen");
     if (v->nnz < 0 || v->nnz > FCOO_MAX_NNZ || v->nseg < 0 || (v->nnz > 0 && v->nseg < 1))
         return fail(FCOO_ERR_INVALID_ARG, "spmttkrp_noalloc: bad nnz/nseg");
+    if (v->nseg > (int64_t)v->dims[v->mode])
+        return fail(FCOO_ERR_INVALID_ARG, "spmttkrp_noalloc: nseg=%lld above dims[mode]=%u", (long long)v->nseg,
+                    v->dims[v->mode]);
     if (dtype != FCOO_F32 && dtype != FCOO_BF16) return fail(FCOO_ERR_INVALID_ARG, "spmttkrp_noalloc: bad dtype");
     if (R < 1) return fail(FCOO_ERR_INVALID_ARG, "spmttkrp_noalloc: R=%d", R);
     if (R > kScratchRank)

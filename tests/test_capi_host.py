@@ -101,6 +101,43 @@ def test_compute_entry_points_reject_null_handles(fc):
     assert lib.fcoo_destroy(None) == 0
 
 
+def test_noalloc_rejects_bad_arguments_without_device_work(fc):
+    # every check of spmttkrp_noalloc runs on the host before any CUDA call,
+    # so fake (never dereferenced) 256-byte-aligned addresses stand in for
+    # the caller's device buffers
+    from paper_1705_09905_gb300 import _lib
+
+    lib = fc.lib
+    fake = 1 << 20
+
+    def view(**kw):
+        v = _lib.FcooView()
+        v.nmodes, v.mode, v.threadlen, v.nnz, v.nseg = 3, 0, 8, 1000, 10
+        for k, d in enumerate((50, 40, 30)):
+            v.dims[k] = d
+        v.pidx[0] = v.pidx[1] = v.val = v.bf = v.sf = v.segrow = v.hcount = fake
+        for k, x in kw.items():
+            setattr(v, k, x)
+        return v
+
+    F = (ctypes.c_void_p * 3)(fake, fake, fake)
+    Fp = ctypes.cast(F, ctypes.POINTER(ctypes.c_void_p))
+
+    def call(v, R=32, out=fake, dtype=0):
+        return lib.spmttkrp_noalloc(ctypes.byref(v), Fp, dtype, R, out, None)
+
+    assert call(view(), out=fake + 2) == _lib.FCOO_ERR_INVALID_ARG  # out not 4-byte aligned
+    assert b"aligned" in lib.fcoo_last_error()
+    assert call(view(), out=None) == _lib.FCOO_ERR_INVALID_ARG
+    assert call(view(mode=3)) == _lib.FCOO_ERR_INVALID_ARG
+    assert call(view(nseg=51)) == _lib.FCOO_ERR_INVALID_ARG  # more segments than rows
+    assert b"nseg" in lib.fcoo_last_error()
+    assert call(view(threadlen=3)) == _lib.FCOO_ERR_INVALID_ARG
+    assert call(view(), dtype=5) == _lib.FCOO_ERR_INVALID_ARG
+    assert call(view(), R=_lib.NOALLOC_MAX_RANK + 8) == _lib.FCOO_ERR_UNSUPPORTED
+    assert b"scratch limit" in lib.fcoo_last_error()
+
+
 def test_header_is_plain_c_and_links(tmp_path):
     """include/fcoo.h compiles as strict C99 and a C program links against
     libfcoo.so and calls it (host-only entry points, and argument errors that

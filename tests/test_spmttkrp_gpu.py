@@ -100,14 +100,20 @@ def test_threadlen_values(fc, oracle, tl):
     run_mttkrp(fc, oracle, T, 32, 0, tl=tl)
 
 
-def test_deterministic_rows_and_output_overwrite(fc, oracle):
-    T = synth.random_small((80, 70, 60), 40_000, seed=4)
-    X, F, a = run_mttkrp(fc, oracle, T, 32, 2)
-    out = torch.full_like(a, float("nan"))
-    b = fc.spmttkrp(X, F, out=out)
-    torch.cuda.synchronize()
-    assert torch.isfinite(b).all()
-    np.testing.assert_allclose(a.cpu().numpy(), b.cpu().numpy(), rtol=1e-6, atol=1e-6)
+@pytest.mark.parametrize("R,dtype", [(32, torch.float32), (16, torch.float32), (64, torch.bfloat16)])
+def test_deterministic_rows_and_output_overwrite(fc, oracle, R, dtype):
+    # the header promises bitwise identical results for repeated calls: a
+    # multi-CTA launch (segments cut by runs and CTAs, carries combined in a
+    # fixed order), compared bit for bit, into an output pre-filled with NaN
+    T = synth.make_tensor(synth.scaled(synth.CONFIGS["skewed3"], 600_001, dims=(800, 700, 900)))
+    X, F, a = run_mttkrp(fc, oracle, T, R, 2, dtype=dtype)
+    assert X.nnz > 64 * 32 * 2  # several CTAs at this size
+    for _ in range(2):
+        out = torch.full_like(a, float("nan"))
+        b = fc.spmttkrp(X, F, out=out)
+        torch.cuda.synchronize()
+        assert torch.isfinite(b).all()
+        assert np.array_equal(a.cpu().numpy().view(np.uint32), b.cpu().numpy().view(np.uint32))
 
 
 # ---------------------------------------------------------------- SpTTM
