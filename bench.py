@@ -170,19 +170,79 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def profile_record():
+    """The committed ncu record of the streaming kernel (SpMTTKRP mode 0 of the
+    skewed workload), if it was taken on the current kernel source, else None."""
+    p = os.path.join(ROOT, "profiles", "k_stream_skewed3_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    return d if d.get("source_hash") == source_hash() else None
+
+
 def traffic_from_profile():
     """dram bytes per launch of the streaming kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "k_stream_skewed3_traffic.json")
-    if not os.path.exists(p):
-        return None, None
-    d = json.load(open(p))
-    if d.get("source_hash") != source_hash():
-        return None, d.get("source_hash")
-    return d.get("traffic_per_launch_full"), d.get("source_hash")
+    d = profile_record()
+    return (d.get("traffic_per_launch_full"), d.get("source_hash")) if d else (None, None)
+
+
+def gather_roof(rec, nnz: int, t_mode: float, sm_mhz, sms: int):
+    """The secondary roofs of the gather-bound streaming kernel, from the
+    committed ncu record (counters per nonzero of one mode-0 launch) and the
+    live per-mode time: the L1 data path (one 128-byte wavefront per SM clock,
+    measured by the gather microbenchmark recorded beside it) and the L2 ->
+    SM traffic against the L2 peak that the same capture implies."""
+    if not rec or "l1_wavefronts" not in rec:
+        return None
+    n = rec["captured_nnz"]
+    wf = rec["l1_wavefronts"] / n
+    clk = (sm_mhz or 2070.0) * 1e6
+    roof_s = wf * nnz / (sms * clk)
+    l2 = rec["lts_bytes"] / n
+    return {"bound": "l1_data_path", "unit": "wavefronts/clk/SM", "peak": 1.0,
+            "wavefronts_per_nnz": wf, "achieved": wf * nnz / (sms * clk * t_mode), "frac": roof_s / t_mode,
+            "l1_hit_rate": rec.get("l1_hit_rate"), "l2_bytes_per_nnz": l2,
+            "l2_GBps": l2 * nnz / t_mode / 1e9, "l2_peak_GBps": rec.get("l2_peak_gbps"),
+            "l2_frac": (l2 * nnz / t_mode / 1e9) / rec["l2_peak_gbps"] if rec.get("l2_peak_gbps") else None,
+            "source": "ncu counters of profiles/k_stream_skewed3_traffic.json (same kernel source), live time"}
 
 
 # ---------------------------------------------------------------- CPU oracle baseline
+
+
+def cpu_baseline_rows(T_host, factors_host, nsample: int, runs: int = 5):
+    """The oracle's SpMTTKRP loop in its multi-threaded build (gcc -O3
+    -fopenmp, every output row summed by one thread; FP64 bitwise equal to
+    the single-threaded oracle) on all host cores, FP64 and FP32 variants, all
+    modes, over the first nsample nonzeros (a uniform random subset: the
+    generator returns nonzeros in random order).  The nonzeros are grouped by
+    row once per mode outside the timing, as the device's F-COO is built once.
+    Returns {variant: (GB/s of the same algorithmic bytes as the device
+    number, median seconds of `runs` runs)} and the thread count."""
+    import oracle
+
+    idx = [a[:nsample] for a in T_host["idx"]]
+    val = T_host["val"][:nsample]
+    dims = T_host["dims"]
+    rows = [oracle.ModeRows(dims, idx, n) for n in range(3)]
+    R = factors_host[0].shape[1]
+    per_nnz = 2 * 4 + 4 + 1 / 8 + 1 / (8 * 8)
+    out = {}
+    for name, fp32 in (("fp64", False), ("fp32", True)):
+        v = val.astype(np.float32) if fp32 else val
+        F = [f.astype(np.float32) for f in factors_host] if fp32 else factors_host
+        elem = 4 if fp32 else 8
+        times = []
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            for n in range(3):
+                oracle.mttkrp_rows(rows[n], v, F, fp32=fp32)
+            times.append(time.perf_counter() - t0)
+        dt = statistics.median(times)
+        b = 3 * nsample * per_nnz + sum(3 * d * R * elem for d in dims)
+        out[name] = (b / dt / 1e9, dt)
+    return out, oracle.num_threads()
 
 
 def oracle_sample_rate(T_host, factors_host, nsample: int):
@@ -204,6 +264,17 @@ def oracle_sample_rate(T_host, factors_host, nsample: int):
 
 
 # ---------------------------------------------------------------- workloads
+
+
+_HOST = {}
+
+
+def host_tensor(T, cfg):
+    """The workload tensor's COO on the host (uint32 indices, FP64 values), once."""
+    if cfg.name not in _HOST:
+        _HOST[cfg.name] = {"dims": cfg.dims, "idx": [a.cpu().numpy().astype(np.uint32) for a in T.idx],
+                           "val": T.val.double().cpu().numpy()}
+    return _HOST[cfg.name]
 
 
 def build_workload(cfg, dev):
@@ -465,7 +536,19 @@ def bench_mttkrp_bf16(fc, Xs, dims, R, steps=50):
             "per_mode_ms": [t * 1e3 for t in per_mode]}
 
 
-def bench_cp_als(fc, Xs, dims, sweeps, R=64, fp32_tail=2, Xttm=None):
+def host_cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (empty if unavailable)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return ""
+
+
+def bench_cp_als(fc, Xs, dims, sweeps, R=64, fp32_tail=2, Xttm=None, T_host=None):
     """CP-ALS, R = 64, `sweeps` sweeps from the same U(0,1) start: FP32 factor
     storage; BF16 storage throughout; and the mixed schedule, BF16 storage for
     all but the last `fp32_tail` sweeps, which run on FP32 storage
@@ -496,13 +579,28 @@ def bench_cp_als(fc, Xs, dims, sweeps, R=64, fp32_tail=2, Xttm=None):
         torch.cuda.synchronize()
         s = st.stats()
         res[name] = {"s_per_iter": a.elapsed_time(b) / 1e3 / (sweeps - 1), "fit": s["fit"], "iters": s["iters"],
-                     "pinv_solves": s["npinv"], "factors": [st.factor(k) for k in range(3)]}
+                     "pinv_solves": s["npinv"], "factors": [st.factor(k).float().cpu() for k in range(3)]}
         st.close()
     out = {"R": R, "sweeps": sweeps, "mixed_schedule": f"BF16 storage for sweeps 1-{sweeps - fp32_tail}, "
                                                         f"FP32 for the last {fp32_tail}"}
     names = [n for n, _ in variants]
     for name in names:
         out[name] = {k: v for k, v in res[name].items() if k != "factors"}
+    if T_host is not None:
+        # Algorithm 1 in FP64 by the oracle (multi-threaded SpMTTKRP loop) from
+        # the same start: the reference the equal-fit reading compares with
+        import oracle
+
+        t0 = time.perf_counter()
+        F, _, fits, npinv = oracle.cp_als_rows(dims, T_host["idx"], T_host["val"],
+                                               [f.double().numpy() for f in init], sweeps)
+        out["oracle_fp64"] = {"fit": float(fits[-1]), "pinv_solves": npinv, "seconds": time.perf_counter() - t0,
+                              "threads": oracle.num_threads()}
+        for name in names:
+            out[name]["fit_diff_vs_oracle"] = abs(res[name]["fit"] - float(fits[-1]))
+            out[name]["factor_rel_vs_oracle"] = [
+                float(np.linalg.norm(res[name]["factors"][k].double().numpy() - F[k]) / np.linalg.norm(F[k]))
+                for k in range(3)]
     for name in names[1:]:
         out[name]["fit_diff_vs_fp32"] = abs(res[name]["fit"] - res["fp32"]["fit"])
         out[name]["factor_rel_vs_fp32"] = [
@@ -512,7 +610,7 @@ def bench_cp_als(fc, Xs, dims, sweeps, R=64, fp32_tail=2, Xttm=None):
     return out
 
 
-def bench_sparse_fit(fc, dev, quick, steps=200):
+def bench_sparse_fit(fc, dev, quick, steps=200, with_oracle=False):
     cfg = synth.CONFIGS["fit3"]
     if quick:
         cfg = synth.scaled(cfg, 1_000_000, dims=(5000, 4000, 3000))
@@ -536,8 +634,24 @@ def bench_sparse_fit(fc, dev, quick, steps=200):
             losses.append(float(loss.item()))
     b.record()
     torch.cuda.synchronize()
-    return {"workload": cfg.note, "steps": steps, "ms_per_step": a.elapsed_time(b) / (steps - 5),
-            "loss_first": losses[0], "loss_last": losses[-1], "optimizer": "Adam lr=1e-2"}
+    out = {"workload": cfg.note, "steps": steps, "ms_per_step": a.elapsed_time(b) / (steps - 5),
+           "loss_first": losses[0], "loss_last": losses[-1], "optimizer": "Adam lr=1e-2",
+           "noise_floor": 0.5 * cfg.nnz * cfg.noise_std ** 2,
+           "rel_residual_last": (2.0 * losses[-1] / float(T.val.double().pow(2).sum())) ** 0.5}
+    if with_oracle:
+        # the device's loss at the final factors against the FP64 oracle's
+        import oracle
+
+        with torch.no_grad():
+            loss_dev = float(fc.SparseCPLoss.apply(Xs, *F).item())
+        idx = [a.cpu().numpy().astype(np.uint32) for a in T.idx]
+        loss_orc, _, _ = oracle.sparse_fit(cfg.dims, idx, T.val.double().cpu().numpy(),
+                                           [f.detach().double().cpu().numpy() for f in F],
+                                           want_dfactors=False, want_dvals=False)
+        out["loss_final_device"] = loss_dev
+        out["loss_final_oracle"] = loss_orc
+        out["loss_rel_diff_vs_oracle"] = abs(loss_dev - loss_orc) / loss_orc
+    return out
 
 
 # ---------------------------------------------------------------- arms
@@ -614,31 +728,92 @@ def run_ours(args):
                    "note": "per step: pinned H2D of the 3 factor matrices, 3 SpMTTKRP calls, D2H of the 3 results; "
                            "F-COO resident (built once, build_s)"}
     if rank == 0 and world == 1 and not args.no_cpu:
-        T_host = {"dims": cfg.dims, "idx": [a.cpu().numpy().astype(np.uint32) for a in T.idx],
-                  "val": T.val.double().cpu().numpy()}
+        T_host = host_tensor(T, cfg)
         Fh = [f.double().cpu().numpy() for f in F]
         nsample = min(cfg.nnz, args.cpu_sample)
-        gbps, dt = oracle_sample_rate(T_host, Fh, nsample)
-        line["cpu_baseline"] = {"value": gbps, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                "sample": f"FP64 C oracle SpMTTKRP, modes 0-2, on the first {nsample} of the "
-                                          f"{cfg.nnz} nonzeros (a uniform random subset), {dt:.1f} s"}
+        rates, threads = cpu_baseline_rows(T_host, Fh, nsample)
+        n1 = min(cfg.nnz, args.cpu_sample_single)
+        gbps1, dt1 = oracle_sample_rate(T_host, Fh, n1)
+        line["cpu_baseline"] = {
+            "value": rates["fp64"][0], "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"the oracle's SpMTTKRP loop (FP64), multi-threaded build (gcc -O3 -fopenmp, each output "
+                      f"row summed by one thread, bitwise the serial oracle), modes 0-2 over the first {nsample} "
+                      f"of the {cfg.nnz} nonzeros (a uniform random subset), {threads} threads, median of 5 runs "
+                      f"({rates['fp64'][1]:.2f} s per run)",
+            "fp32": {"value": rates["fp32"][0], "unit": "GB/s", "s_per_run": rates["fp32"][1],
+                     "note": "same loop with FP32 values, factors and sums"},
+            "cpu_count": os.cpu_count(), "cpu_model": host_cpu_model(),
+            "single_thread_oracle": {"value": gbps1, "unit": "GB/s", "cores": 1,
+                                     "sample": f"the FP64 oracle as the tests use it (gcc -O2, one thread), "
+                                               f"first {n1} nonzeros, {dt1:.1f} s"}}
+    g = gather_roof(profile_record(), cfg.nnz, per_mode[0], clocks.get("sm_mhz"),
+                    torch.cuda.get_device_properties(dev).multi_processor_count)
+    if g:
+        line["roofline"]["gather"] = g
     if not args.no_extras and rank == 0:
         for name, fn in (("mttkrp_bf16", lambda: bench_mttkrp_bf16(fc, Xs, cfg.dims, R)),
                          ("spttm", lambda: bench_spttm(fc, dev, args.quick)),
                          ("spttmc", lambda: bench_spttmc(fc, Xs, cfg.dims, dev, T)),
                          ("tucker", lambda: bench_tucker(fc, Xs, cfg.dims)),
                          ("cp_als", lambda: bench_cp_als(fc, Xs, cfg.dims, 20 if not args.quick else 5,
-                                                         Xttm=ttm_handle(fc, T, cfg.dims, 2))),
-                         ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick))):
+                                                         Xttm=ttm_handle(fc, T, cfg.dims, 2),
+                                                         T_host=None if args.no_cpu else host_tensor(T, cfg))),
+                         ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick, with_oracle=not args.no_cpu))):
             try:
                 line[name] = fn()
             except Exception as e:  # reported, not hidden
                 line[name] = {"error": f"{type(e).__name__}: {e}"}
             torch.cuda.synchronize()
+    if not args.no_extras and rank == 0:
+        line["summary"] = summarize(line)  # last: the part of the line a short tail shows
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.destroy_process_group()
+
+
+def summarize(line):
+    """The headline of every extra result, compact, for the end of the line."""
+    out = {}
+
+    def get(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    def r(x, n=4):
+        return round(x, n) if isinstance(x, float) else x
+
+    if "spttm" in line:
+        t = line["spttm"]
+        out["spttm_4way_mode3"] = {"ms": r(get(t, "ms")), "GBps": r(get(t, "GBps"), 1),
+                                   "pct_hbm": r(get(t, "GBps") / peaks()[0]) if get(t, "GBps") else None,
+                                   "nfib": get(t, "nfib")}
+    if "mttkrp_bf16" in line:
+        t = line["mttkrp_bf16"]
+        out["spmttkrp_bf16_R32"] = {"ms_per_step": r(get(t, "ms_per_step")), "GBps": r(get(t, "GBps"), 1)}
+    if "cp_als" in line:
+        c = line["cp_als"]
+        out["cp_als_R64_20"] = {
+            k: {"s_per_iter": r(get(c, k, "s_per_iter"), 6), "fit": r(get(c, k, "fit"), 7),
+                "fit_diff_vs_oracle": r(get(c, k, "fit_diff_vs_oracle"), 8),
+                "factor_rel_vs_oracle": [r(x) for x in (get(c, k, "factor_rel_vs_oracle") or [])]}
+            for k in ("fp32", "bf16", "mixed") if k in c}
+        out["cp_als_R64_20"]["oracle_fit"] = r(get(c, "oracle_fp64", "fit"), 7)
+        out["cp_als_R64_20"]["mixed_speedup_vs_fp32"] = r(get(c, "mixed", "speedup_vs_fp32"), 3)
+    if "sparse_fit" in line:
+        f = line["sparse_fit"]
+        out["sparse_fit"] = {"ms_per_step": r(get(f, "ms_per_step")), "loss_first": r(get(f, "loss_first"), 1),
+                             "loss_last": r(get(f, "loss_last"), 1), "noise_floor": r(get(f, "noise_floor"), 1),
+                             "loss_rel_diff_vs_oracle": r(get(f, "loss_rel_diff_vs_oracle"), 9)}
+    if "spttmc" in line:
+        out["spttmc_mode0_TFLOPs"] = {str(x.get("R")): r(get(x, "modes")[0].get("TFLOPs"), 2)
+                                      for x in get(line, "spttmc", "ranks") or []}
+    if "tucker" in line:
+        out["tucker_R8_ms_per_iter"] = r(get(line, "tucker", "ms_per_iter"), 3)
+    return out
 
 
 def run_reference(args):
@@ -687,6 +862,7 @@ def main():
     ap.add_argument("--nnz", type=int, default=0, help="scale the workload to this many nonzeros (same dims)")
     ap.add_argument("--rank", type=int, default=0, help="override R")
     ap.add_argument("--cpu-sample", type=int, default=40_000_000)
+    ap.add_argument("--cpu-sample-single", type=int, default=4_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
     ap.add_argument("--part", default="all", choices=["all", "spttm", "spttmc", "tucker", "cp", "fit", "sweep"],
                     help="only one extra line, for profiling: spttm (4-way workload, --nnz scales it), "
@@ -718,7 +894,8 @@ def main():
         else:
             cfg = workload_config(args)
             T, Xs, _, _ = build_workload(cfg, dev)
-            line = bench_cp_als(fc, Xs, cfg.dims, args.sweeps, Xttm=ttm_handle(fc, T, cfg.dims, 2))
+            line = bench_cp_als(fc, Xs, cfg.dims, args.sweeps, Xttm=ttm_handle(fc, T, cfg.dims, 2),
+                                T_host=host_tensor(T, cfg))
         print(json.dumps(line), flush=True)
         return
     if args.impl == "reference":

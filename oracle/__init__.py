@@ -19,6 +19,12 @@ for the passage of the paper each routine follows:
 * ``spd_solve``     -- the ``V^dagger`` of Algorithm 1 (Cholesky / pinv)
 * ``sparse_fit``    -- loss and gradients of the observed-entry CP fit
 * ``mttkrp_adjoint``-- adjoint of Eq. 6 for a given output cotangent
+* ``mttkrp_rows``   -- the SpMTTKRP loop of ``mttkrp`` with each output row
+                       summed by one OpenMP thread (``fcoo_oracle_omp.c``,
+                       gcc -O3 -fopenmp): bitwise equal to ``mttkrp`` in FP64;
+                       an FP32 variant times the FP32 CPU baseline
+* ``cp_als_rows``   -- Algorithm 1 as ``cp_als``, its MTTKRPs by
+                       ``mttkrp_rows``, for runs too large for one core
 
 Parity status: all functions pinned (see tests/test_oracle_pins.py).
 """
@@ -35,8 +41,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fcoo_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_SRC_OMP = os.path.join(_HERE, "fcoo_oracle_omp.c")
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _f64p = ctypes.POINTER(ctypes.c_double)
@@ -52,6 +61,30 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile liboracle_omp.so (the multi-threaded SpMTTKRP loop) with gcc
+    -O3 -fopenmp; contraction into FMAs is off, as in the ISO C99 build of
+    liboracle.so, so both round every product and sum alike."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO_OMP) or os.path.getmtime(_SO_OMP) < os.path.getmtime(_SRC_OMP):
+        tmp = _SO_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                               tmp, _SRC_OMP])
+        os.replace(tmp, _SO_OMP)
+    return _SO_OMP
+
+
+def _load_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            lib = ctypes.CDLL(build_omp())
+            for f in ("orp_num_threads", "orp_mode_rows", "orp_mttkrp_f64", "orp_mttkrp_f32"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib_omp = lib
+    return _lib_omp
 
 
 def _load():
@@ -314,3 +347,88 @@ def hooi(dims, idx, val, init_factors, iters):
         g2 = float(np.sum(sig2))
         fits.append(1.0 - np.sqrt(max(0.0, x2 - g2)) / np.sqrt(x2))
     return F, fits
+
+
+# ---------------------------------------------------------------- multi-threaded loop
+
+
+def num_threads() -> int:
+    """Threads the OpenMP build runs on (OMP_NUM_THREADS, else all cores)."""
+    return int(_load_omp().orp_num_threads())
+
+
+class ModeRows:
+    """The nonzeros of a COO tensor grouped by their index in ``mode`` (stable:
+    each row keeps its nonzeros in input order): rowptr (dims[mode] + 1) and
+    order (nnz), for ``mttkrp_rows``."""
+
+    def __init__(self, dims, idx, mode):
+        lib = _load_omp()
+        self.coo = _Coo(dims, idx)
+        self.mode = int(mode)
+        self.rowptr = np.empty(int(self.coo.dims[mode]) + 1, dtype=np.int64)
+        self.order = np.empty(max(self.coo.nnz, 1), dtype=np.int64)
+        _check(lib.orp_mode_rows(ctypes.c_int64(self.coo.nnz), self.coo.idx[mode].ctypes.data_as(_u32p),
+                                 ctypes.c_uint32(int(self.coo.dims[mode])), self.rowptr.ctypes.data_as(_i64p),
+                                 self.order.ctypes.data_as(_i64p)))
+
+
+def mttkrp_rows(rows: ModeRows, val, factors, fp32: bool = False):
+    """SpMTTKRP (Eq. 6) on rows.mode with every output row summed by one
+    thread: FP64 (bitwise equal to ``mttkrp``), or with FP32 values, factors
+    and sums when fp32 is set.  Returns dims[mode] x R."""
+    lib = _load_omp()
+    c, mode = rows.coo, rows.mode
+    R = int(np.asarray(factors[(mode + 1) % c.nmodes]).shape[1])
+    if fp32:
+        dt, ptr, fn = np.float32, ctypes.POINTER(ctypes.c_float), lib.orp_mttkrp_f32
+    else:
+        dt, ptr, fn = np.float64, _f64p, lib.orp_mttkrp_f64
+    val = np.ascontiguousarray(np.asarray(val, dtype=dt))
+    fs = [(np.ascontiguousarray(np.asarray(f, dtype=dt)) if k != mode else np.zeros((1, R), dt))
+          for k, f in enumerate(factors)]
+    table = (ptr * len(fs))(*[f.ctypes.data_as(ptr) for f in fs])
+    out = np.empty((int(c.dims[mode]), R), dtype=dt)
+    _check(fn(c.nmodes, c.dims_ptr, c.idx_ptrs, val.ctypes.data_as(ptr), table, R, mode,
+              rows.rowptr.ctypes.data_as(_i64p), rows.order.ctypes.data_as(_i64p), out.ctypes.data_as(ptr)))
+    return out
+
+
+def cp_als_rows(dims, idx, val, init_factors, iters, rows=None):
+    """Algorithm 1 for ``iters`` sweeps from ``init_factors``, the steps of
+    ``cp_als`` in its order: M = SpMTTKRP_n (``mttkrp_rows``, FP64), V = the
+    Hadamard product of the other modes' Grams, F_n = M V^dagger
+    (``spd_solve``), columns normalised by their 2-norms (lambda = the norms of
+    the last mode), and after each sweep fit = 1 - sqrt(max(0, |X|^2 +
+    lambda^T (Hadamard of all Grams) lambda - 2 <X, Xhat>)) / |X| with
+    <X, Xhat> = sum_r lambda_r sum_i M_last(i, r) F_last(i, r).  ``rows``: one
+    ModeRows per mode (built here if None).  Returns (factors, lambda, fits,
+    number of pseudo-inverse solves)."""
+    N = len(dims)
+    val = _f64(val)
+    rows = rows or [ModeRows(dims, idx, n) for n in range(N)]
+    F = [_f64(f).copy() for f in init_factors]
+    R = F[0].shape[1]
+    x2 = float(np.dot(val, val))
+    lam = np.ones(R)
+    fits, npinv = [], 0
+    M = None
+    for _ in range(iters):
+        for n in range(N):
+            M = mttkrp_rows(rows[n], val, F)
+            V = np.ones((R, R))
+            for k in range(N):
+                if k != n:
+                    V *= gram(F[k])
+            F[n], used = spd_solve(V, M)
+            npinv += int(used)
+            nrm = np.sqrt(np.einsum("ir,ir->r", F[n], F[n]))
+            lam = nrm.copy()
+            F[n] = np.where(nrm > 0, F[n] / np.where(nrm > 0, nrm, 1.0), F[n])
+        V = np.ones((R, R))
+        for k in range(N):
+            V *= gram(F[k])
+        xhat2 = float(lam @ V @ lam)
+        inner = float(np.dot(lam, np.einsum("ir,ir->r", M, F[N - 1])))
+        fits.append(1.0 - np.sqrt(max(0.0, x2 + xhat2 - 2.0 * inner)) / np.sqrt(x2))
+    return F, lam, np.array(fits), npinv

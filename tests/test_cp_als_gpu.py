@@ -38,12 +38,20 @@ def test_fp32_sweeps_match_oracle(fc, oracle):
         st.iterate(Xs)
         s = st.stats()
         for n in range(3):
+            # the bound below rests on well-conditioned normal equations: the
+            # FP32 rounding of M (about 1e-7) moves the solution by at most
+            # cond(V) times that; measured cond(V) <= 14 on this case
+            V = np.ones((R, R))
+            for k in range(3):
+                if k != n:
+                    V *= oracle.gram(F[k])
+            assert np.linalg.cond(V) <= 100, (sweep, n, np.linalg.cond(V))
             F, lam, _, _ = oracle.cp_als_mode(T.dims, idx, val, F, n)
         ref_fit = oracle.cp_fit(T.dims, idx, val, F, lam)
         assert abs(s["fit"] - ref_fit) <= 1e-5, (sweep, s["fit"], ref_fit)
-        assert rel_fro(s["lambda"], lam) <= 1e-4
+        assert rel_fro(s["lambda"], lam) <= 1e-5
         for k in range(3):
-            assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 1e-4, (sweep, k)
+            assert rel_fro(st.factor(k).cpu().numpy(), F[k]) <= 1e-5, (sweep, k)
         fits.append(s["fit"])
         assert s["iters"] == sweep + 1
     assert all(b >= a - 1e-6 for a, b in zip(fits, fits[1:])), fits

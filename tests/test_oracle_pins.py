@@ -557,3 +557,48 @@ def test_cp_als_mode_steps_compose_to_a_sweep_and_fit_matches_dense(oracle):
     X = densify(dims, idx, val)
     direct = 1.0 - np.linalg.norm(X - dense_kruskal(lam, F)) / np.linalg.norm(X)
     np.testing.assert_allclose(fit, direct, rtol=1e-10)
+
+
+# ---------------------------------------------------------------- multi-threaded build
+
+
+@pytest.mark.parametrize("dims", [(40, 30, 20), (9, 8, 7, 6)])
+def test_mttkrp_rows_is_bitwise_the_oracle_loop(oracle, dims):
+    # each output row summed by one thread, in input order, is the serial
+    # loop term for term: equal bit for bit in FP64, on every mode (empty
+    # slices, a hot slice and a single-nonzero slice included)
+    rng = np.random.default_rng(3)
+    n = 3000
+    idx = [rng.integers(0, d, size=n).astype(np.uint32) for d in dims]
+    idx[0][:500] = 2  # one hot slice
+    idx[0][500] = dims[0] - 1  # a slice with one nonzero
+    idx[0][501:] %= max(dims[0] - 2, 1)  # the slice dims[0] - 2 stays empty
+    val = rng.standard_normal(n)
+    F = [rng.standard_normal((d, 7)) for d in dims]
+    for mode in range(len(dims)):
+        rows = oracle.ModeRows(dims, idx, mode)
+        a = oracle.mttkrp(dims, idx, val, F, mode)
+        b = oracle.mttkrp_rows(rows, val, F)
+        assert np.array_equal(a, b), mode
+        c = oracle.mttkrp_rows(rows, val.astype(np.float32), [f.astype(np.float32) for f in F], fp32=True)
+        absref = oracle.mttkrp(dims, idx, np.abs(val), [np.abs(f) for f in F], mode)
+        assert np.all(np.abs(c - a) <= 1e-5 * absref + 1e-30), mode  # FP32 sums of at most 3000 terms
+
+
+def test_cp_als_rows_matches_cp_als(oracle):
+    # Algorithm 1 driven from Python over the multi-threaded loop: the same
+    # sweeps as the C oracle
+    rng = np.random.default_rng(4)
+    dims = (30, 25, 20)
+    n = 4000
+    lin = rng.choice(np.prod(dims), size=n, replace=False)
+    idx = [a.astype(np.uint32) for a in np.unravel_index(lin, dims)]
+    val = rng.random(n)
+    init = [rng.random((d, 6)) for d in dims]
+    f1, l1, fit1, p1 = oracle.cp_als(dims, idx, val, init, 6)
+    f2, l2, fit2, p2 = oracle.cp_als_rows(dims, idx, val, init, 6)
+    assert np.max(np.abs(fit1 - fit2)) <= 1e-12
+    assert p1 == p2
+    assert np.max(np.abs(l1 - l2)) <= 1e-10 * np.max(np.abs(l1))
+    for a, b in zip(f1, f2):
+        assert np.max(np.abs(a - b)) <= 1e-10
