@@ -64,14 +64,23 @@ def peaks():
 def mttkrp_alg_bytes(X, R: int, elem: int) -> int:
     """Compulsory bytes of one SpMTTKRP call: the Table II stream, the segment
     map, every factor row of the product modes read once, the output written once."""
-    b = X.bytes["table2"] + X.bytes["segmap"]
+    b = table2_read(X) + X.bytes["segmap"]
     b += sum(X.dims[k] * R * elem for k in X.prod_modes)
     b += X.dims[X.mode] * R * 4
     return int(b)
 
 
+def table2_read(X) -> int:
+    """Table II bytes the kernels read: with 16-bit product-mode indices once
+    the handle is compressed (2 instead of 4 bytes per index)."""
+    b = X.bytes["table2"]
+    if X.bytes.get("pidx16"):
+        b += X.bytes["pidx16"] - X.bytes["pidx"]
+    return int(b)
+
+
 def ttm_alg_bytes(X, R: int, elem: int) -> int:
-    return int(X.bytes["table2"] + X.dims[X.mode] * R * elem + X.nseg * R * 4)
+    return int(table2_read(X) + X.dims[X.mode] * R * elem + X.nseg * R * 4)
 
 
 class Clocks:
@@ -370,8 +379,15 @@ def bench_spttm(fc, dev, quick, nnz=0):
     torch.cuda.synchronize()
     t = a.elapsed_time(b) / 1e3 / n
     byt = ttm_alg_bytes(X, 16, 4)
-    return {"workload": cfg.note, "nnz": X.nnz, "nfib": X.nseg, "R": 16, "ms": t * 1e3,
-            "alg_bytes": byt, "GBps": byt / t / 1e9, "GFLOPs": 2 * 16 * X.nnz / t / 1e9}
+    res = {"workload": cfg.note, "nnz": X.nnz, "nfib": X.nseg, "R": 16, "ms": t * 1e3,
+           "alg_bytes": byt, "GBps": byt / t / 1e9, "GFLOPs": 2 * 16 * X.nnz / t / 1e9}
+    # the same with 16-bit indices (the product mode has 50,000 rows): its own,
+    # smaller algorithmic bytes
+    X.compress_indices()
+    t16 = _time_calls(lambda: fc.spttm(X, U, out=out))
+    b16 = ttm_alg_bytes(X, 16, 4)
+    res["idx16"] = {"ms": t16 * 1e3, "alg_bytes": b16, "GBps": b16 / t16 / 1e9, "speedup": t / t16}
+    return res
 
 
 def ttmc_alg_bytes(X, R: int) -> int:
@@ -546,6 +562,25 @@ def host_cpu_model() -> str:
     except Exception:
         pass
     return ""
+
+
+def bench_mttkrp_idx16(fc, Xs, dims, R, steps=50):
+    """The headline's three SpMTTKRP calls after index compression (16-bit
+    product-mode indices, every dimension <= 65,536), against the same calls
+    on the same handles before it: ms per mode, and GB/s of each form's own
+    algorithmic bytes (8.14 instead of 12.14 bytes of stream per nonzero)."""
+    dev = torch.device("cuda")
+    F = [f.to(dev) for f in synth.make_factors(dims, R, seed=1)]
+    outs = [torch.empty((dims[n], R), device=dev) for n in range(3)]
+    tot32, pm32 = time_spmttkrp(fc, Xs, F, outs, steps, 5, torch.cuda.current_stream())
+    alg32 = [mttkrp_alg_bytes(Xs[n], R, 4) for n in range(3)]
+    for X in Xs:
+        X.compress_indices()
+    tot16, pm16 = time_spmttkrp(fc, Xs, F, outs, steps, 5, torch.cuda.current_stream())
+    alg16 = [mttkrp_alg_bytes(Xs[n], R, 4) for n in range(3)]
+    return {"R": R, "per_mode_ms_idx32": [t * 1e3 for t in pm32], "per_mode_ms_idx16": [t * 1e3 for t in pm16],
+            "GBps_idx32": sum(alg32) * steps / tot32 / 1e9, "GBps_idx16": sum(alg16) * steps / tot16 / 1e9,
+            "alg_bytes_per_step_idx16": sum(alg16), "speedup": tot32 / tot16}
 
 
 def bench_cp_als(fc, Xs, dims, sweeps, R=64, fp32_tail=2, Xttm=None, T_host=None):
@@ -758,7 +793,9 @@ def run_ours(args):
                          ("cp_als", lambda: bench_cp_als(fc, Xs, cfg.dims, 20 if not args.quick else 5,
                                                          Xttm=ttm_handle(fc, T, cfg.dims, 2),
                                                          T_host=None if args.no_cpu else host_tensor(T, cfg))),
-                         ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick, with_oracle=not args.no_cpu))):
+                         ("sparse_fit", lambda: bench_sparse_fit(fc, dev, args.quick, with_oracle=not args.no_cpu)),
+                         # last: it compresses the workload's handles in place
+                         ("mttkrp_idx16", lambda: bench_mttkrp_idx16(fc, Xs, cfg.dims, R))):
             try:
                 line[name] = fn()
             except Exception as e:  # reported, not hidden
@@ -791,6 +828,14 @@ def summarize(line):
         out["spttm_4way_mode3"] = {"ms": r(get(t, "ms")), "GBps": r(get(t, "GBps"), 1),
                                    "pct_hbm": r(get(t, "GBps") / peaks()[0]) if get(t, "GBps") else None,
                                    "nfib": get(t, "nfib")}
+    if "mttkrp_idx16" in line:
+        t = line["mttkrp_idx16"]
+        out["spmttkrp_idx16_R32"] = {"ms_per_mode": [r(x) for x in get(t, "per_mode_ms_idx16") or []],
+                                     "ms_per_mode_idx32": [r(x) for x in get(t, "per_mode_ms_idx32") or []],
+                                     "GBps": r(get(t, "GBps_idx16"), 1), "speedup": r(get(t, "speedup"), 3)}
+    if "spttm" in line and "idx16" in line["spttm"]:
+        t = line["spttm"]["idx16"]
+        out["spttm_idx16"] = {"ms": r(get(t, "ms")), "GBps": r(get(t, "GBps"), 1), "speedup": r(get(t, "speedup"), 3)}
     if "mttkrp_bf16" in line:
         t = line["mttkrp_bf16"]
         out["spmttkrp_bf16_R32"] = {"ms_per_step": r(get(t, "ms_per_step")), "GBps": r(get(t, "GBps"), 1)}

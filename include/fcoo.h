@@ -83,6 +83,8 @@ typedef struct {
     int64_t bytes_segmap;  /* segment -> output row / fibre index tuples     */
     int64_t bytes_aux;     /* segment counts per 1024 nonzeros, permutation  */
     int64_t bytes_scratch; /* carry buffers used by the kernels              */
+    int64_t bytes_pidx16;  /* 16-bit product-mode index streams, 2 B/nnz each
+                              (0 unless fcoo_compress_indices was called)   */
 } fcoo_info_t;
 
 /* ---------------------------------------------------------------------- */
@@ -106,6 +108,12 @@ int fcoo_version(void);
  * multiple of 32*threadlen this is exactly (4 + 4*nprod + 1/8 +
  * 1/(8*threadlen)) * nnz.  Returns -1 on bad arguments. */
 int64_t fcoo_table2_bytes(int nprod, int64_t nnz, int threadlen);
+
+/* The same with `index_bytes` (4 or 2) bytes per product-mode index: the
+ * Table II arrays of a handle after fcoo_compress_indices (index_bytes = 2)
+ * are 4*nnz + 2*nprod*nnz + the two flag arrays.  Returns -1 on bad
+ * arguments. */
+int64_t fcoo_table2_bytes_ex(int nprod, int64_t nnz, int threadlen, int index_bytes);
 
 /* ---------------------------------------------------------------------- */
 /* F-COO construction (Sec. IV-B, Table I, Table II, Fig. 2; host          */
@@ -164,6 +172,21 @@ int fcoo_info(const fcoo_t *X, fcoo_info_t *info);
  *   val      nnz float32 values in F-COO order */
 int fcoo_copy_layout(const fcoo_t *X, uint32_t *perm, uint32_t *bf, uint32_t *sf, uint32_t *segkeys,
                      uint32_t *pidx, float *val, fcoo_stream_t stream);
+
+/* Index compression (Table II with 16-bit indices): adds to the handle a copy
+ * of every product-mode index stream in 16 bits (2 bytes per nonzero and
+ * stream instead of 4), allowed when every product-mode dimension is at most
+ * 65,536.  Afterwards spmttkrp and spttm read these streams wherever their
+ * kernel takes them: 3-way SpMTTKRP and SpTTM of any order, with factor rows
+ * of eight FP32 or BF16 columns per lane (R a multiple of 8, rows 32-byte
+ * (FP32) or 16-byte (BF16) aligned) or four FP32 columns per lane (R = 4..16
+ * in steps of 4, rows 16-byte aligned).  Other calls and shapes keep reading the
+ * 32-bit streams, which stay in the handle.  The results are bitwise equal
+ * to those from the 32-bit streams (same reduction order).  Calling it again
+ * is a no-op.  Synchronous.  Errors: FCOO_ERR_INVALID_ARG (NULL handle),
+ * FCOO_ERR_UNSUPPORTED (a product-mode dimension above 65,536),
+ * FCOO_ERR_NOMEM, FCOO_ERR_CUDA. */
+int fcoo_compress_indices(fcoo_t *X, fcoo_stream_t stream);
 
 /* Index tuples of the SpTTM output fibres (the semi-sparse result of Eq. 3,
  * Sec. II): nseg rows of (N-1) uint32, in output-row order, written to host

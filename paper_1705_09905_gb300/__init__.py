@@ -61,9 +61,10 @@ def _as_f32(a):
     return arr.ctypes.data, arr
 
 
-def table2_bytes(nprod: int, nnz: int, threadlen: int) -> int:
-    """Bytes of the Table II arrays for ``nnz`` nonzeros (host only)."""
-    return int(lib.fcoo_table2_bytes(nprod, nnz, threadlen))
+def table2_bytes(nprod: int, nnz: int, threadlen: int, index_bytes: int = 4) -> int:
+    """Bytes of the Table II arrays for ``nnz`` nonzeros with ``index_bytes``
+    (4, or 2 after index compression) per product-mode index (host only)."""
+    return int(lib.fcoo_table2_bytes_ex(nprod, nnz, threadlen, index_bytes))
 
 
 class FCOO:
@@ -84,7 +85,8 @@ class FCOO:
         self.prod_modes = tuple(int(info.prod_modes[k]) for k in range(info.nprod))
         self.idx_modes = tuple(int(info.idx_modes[k]) for k in range(info.nidx))
         self.bytes = {k: int(getattr(info, "bytes_" + k)) for k in
-                      ("val", "pidx", "bf", "sf", "table2", "segmap", "aux", "scratch")}
+                      ("val", "pidx", "bf", "sf", "table2", "segmap", "aux", "scratch", "pidx16")}
+        self.compressed = self.bytes["pidx16"] > 0
 
     @classmethod
     def build(cls, idx: Sequence, val, dims: Sequence[int], mode: int, op="mttkrp", threadlen: int = 8,
@@ -126,6 +128,17 @@ class FCOO:
             self.close()
         except Exception:
             pass
+
+    def compress_indices(self, stream=None) -> "FCOO":
+        """Add 16-bit copies of the product-mode index streams (every
+        product-mode dimension <= 65,536); SpMTTKRP and SpTTM then read them
+        where their kernel takes them (Table II with 2-byte indices)."""
+        check(lib.fcoo_compress_indices(self._h, _stream(stream) if torch.cuda.is_available() else None))
+        info = FcooInfo()
+        check(lib.fcoo_info(self._h, ctypes.byref(info)))
+        self.bytes["pidx16"] = int(info.bytes_pidx16)
+        self.compressed = True
+        return self
 
     def layout(self) -> dict:
         """Copy the F-COO arrays to host numpy arrays."""

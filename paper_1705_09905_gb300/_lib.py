@@ -41,7 +41,7 @@ class FcooInfo(ctypes.Structure):
         ("nidx", ctypes.c_int), ("idx_modes", ctypes.c_int * MAX_MODES),
         ("bytes_val", ctypes.c_int64), ("bytes_pidx", ctypes.c_int64), ("bytes_bf", ctypes.c_int64),
         ("bytes_sf", ctypes.c_int64), ("bytes_table2", ctypes.c_int64), ("bytes_segmap", ctypes.c_int64),
-        ("bytes_aux", ctypes.c_int64), ("bytes_scratch", ctypes.c_int64),
+        ("bytes_aux", ctypes.c_int64), ("bytes_scratch", ctypes.c_int64), ("bytes_pidx16", ctypes.c_int64),
     ]
 
 
@@ -69,6 +69,8 @@ SIGNATURES = {
     "fcoo_status_string": (ctypes.c_char_p, [_i]),
     "fcoo_version": (_i, []),
     "fcoo_table2_bytes": (_i64, [_i, _i64, _i]),
+    "fcoo_table2_bytes_ex": (_i64, [_i, _i64, _i, _i]),
+    "fcoo_compress_indices": (_i, [_vp, _vp]),
     "fcoo_build": (_i, [_i, _vp, _i64, _vpp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_vp)]),
     "fcoo_destroy": (_i, [_vp]),
     "fcoo_info": (_i, [_vp, ctypes.POINTER(FcooInfo)]),

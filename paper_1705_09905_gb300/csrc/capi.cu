@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "internal.cuh"
@@ -75,6 +76,15 @@ int num_sms() {
     return n > 0 ? n : 1;
 }
 
+// Two 32-bit indices (each < 65,536) -> one word of two 16-bit indices, the
+// lower position in the low half.
+__global__ void k_narrow_u16(const uint32_t *in, int64_t n2, uint32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 v = reinterpret_cast<const uint2 *>(in)[i];
+        out[i] = (v.x & 0xffffu) | (v.y << 16);
+    }
+}
+
 int device_sms(int dev) {
     static std::atomic<int> cache[kMaxDevices];
     if (dev < 0 || dev >= kMaxDevices) return num_sms();
@@ -88,7 +98,10 @@ int device_sms(int dev) {
 
 void stream_params_from(const fcoo_t *X, StreamParams &p) {
     memset(&p, 0, sizeof(p));
-    for (int m = 0; m < X->nprod; ++m) p.pidx[m] = X->pidx[m];
+    for (int m = 0; m < X->nprod; ++m) {
+        p.pidx[m] = X->pidx[m];
+        p.pidx16[m] = X->pidx16[m];
+    }
     p.val = X->val;
     p.bf = X->bf;
     p.sf = X->sf;
@@ -131,12 +144,16 @@ const char *fcoo_status_string(int status) {
 
 int fcoo_version(void) { return 10000; }
 
-int64_t fcoo_table2_bytes(int nprod, int64_t nnz, int threadlen) {
-    if (nprod < 1 || nprod >= FCOO_MAX_MODES || nnz < 0 ||
-        threadlen < 1 || threadlen > 64 || (threadlen & (threadlen - 1)) != 0)
+int64_t fcoo_table2_bytes_ex(int nprod, int64_t nnz, int threadlen, int index_bytes) {
+    if (nprod < 1 || nprod >= FCOO_MAX_MODES || nnz < 0 || threadlen < 1 || threadlen > 64 ||
+        (threadlen & (threadlen - 1)) != 0 || (index_bytes != 4 && index_bytes != 2))
         return -1;
     int64_t npart = ceil_div(nnz, threadlen);
-    return 4 * nnz + 4 * (int64_t)nprod * nnz + 4 * ceil_div(nnz, 32) + 4 * ceil_div(npart, 32);
+    return 4 * nnz + (int64_t)index_bytes * nprod * nnz + 4 * ceil_div(nnz, 32) + 4 * ceil_div(npart, 32);
+}
+
+int64_t fcoo_table2_bytes(int nprod, int64_t nnz, int threadlen) {
+    return fcoo_table2_bytes_ex(nprod, nnz, threadlen, 4);
 }
 
 int fcoo_destroy(fcoo_t *X) {
@@ -147,6 +164,7 @@ int fcoo_destroy(fcoo_t *X) {
     dev_free(X->grad_scratch);
     dev_free(X->gmap);
     dev_free(X->base);
+    dev_free(X->base16);
     free(X);
     return FCOO_OK;
 }
@@ -175,6 +193,7 @@ int fcoo_info(const fcoo_t *X, fcoo_info_t *info) {
     info->bytes_segmap = X->bytes_segmap;
     info->bytes_aux = X->bytes_aux;
     info->bytes_scratch = X->bytes_scratch;
+    info->bytes_pidx16 = X->base16 ? 2 * (int64_t)X->nprod * X->nnz : 0;
     return FCOO_OK;
 }
 
@@ -195,6 +214,36 @@ int fcoo_copy_layout(const fcoo_t *X, uint32_t *perm, uint32_t *bf, uint32_t *sf
             FCOO_CUDA(cudaMemcpyAsync(pidx + m * n, X->pidx[m], n * 4, cudaMemcpyDefault, s));
     if (val && n) FCOO_CUDA(cudaMemcpyAsync(val, X->val, n * 4, cudaMemcpyDefault, s));
     FCOO_CUDA(cudaStreamSynchronize(s));
+    return FCOO_OK;
+}
+
+int fcoo_compress_indices(fcoo_t *X, fcoo_stream_t stream) {
+    clear_error();
+    if (!X) return fail(FCOO_ERR_INVALID_ARG, "fcoo_compress_indices: NULL handle");
+    if (X->base16) return FCOO_OK;
+    for (int m = 0; m < X->nprod; ++m)
+        if (X->dims[X->prod_modes[m]] > 65536u)
+            return fail(FCOO_ERR_UNSUPPORTED, "fcoo_compress_indices: product mode %d has dimension %u > 65536",
+                        X->prod_modes[m], X->dims[X->prod_modes[m]]);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t npad = X->npad;
+    void *b = nullptr;
+    FCOO_CUDA(dev_alloc(&b, (size_t)npad * 2 * X->nprod));
+    uint16_t *out[FCOO_MAX_MODES] = {};
+    for (int m = 0; m < X->nprod; ++m) out[m] = static_cast<uint16_t *>(b) + (size_t)m * npad;
+    for (int m = 0; m < X->nprod; ++m) {
+        const int64_t n2 = npad / 2;  // two indices per thread, npad is even
+        k_narrow_u16<<<(unsigned)std::min<int64_t>(ceil_div(n2, 256), (int64_t)num_sms() * 16), 256, 0, s>>>(
+            X->pidx[m], n2, reinterpret_cast<uint32_t *>(out[m]));
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            dev_free(b);
+            return cuda_fail(e, "fcoo_compress_indices");
+        }
+    }
+    for (int m = 0; m < X->nprod; ++m) X->pidx16[m] = out[m];
+    X->base16 = b;
     return FCOO_OK;
 }
 

@@ -67,6 +67,10 @@ struct fcoo {
     uint32_t *segkeys;               // nseg x nidx index-mode tuples
     uint32_t *hcount;                // heads before chunk c (kChunk nonzeros each), nchunk+1
     uint32_t *perm;                  // npad: original COO position of each nonzero
+    // 16-bit copies of the product-mode streams (fcoo_compress_indices), in
+    // one allocation of nprod * npad uint16; NULL until compressed
+    uint16_t *pidx16[FCOO_MAX_MODES];
+    void *base16;
     // kernel scratch: carry partials (FP64) and their segment ids, and the
     // arrival counter of the last-CTA combine
     double *carry_val;
@@ -92,6 +96,7 @@ namespace fcx {
 // SpTTM, and the adjoint passes, which are SpMTTKRP-shaped).
 struct StreamParams {
     const uint32_t *pidx[FCOO_MAX_MODES - 1];  // product-mode streams
+    const uint16_t *pidx16[FCOO_MAX_MODES - 1];  // the same in 16 bits, or NULL
     const void *F[FCOO_MAX_MODES - 1];         // matching dense rows (dtype)
     const float *val;                          // values (or per-nonzero weights)
     const uint32_t *bf, *sf, *hcount;

@@ -35,10 +35,13 @@
 //     (FMUL2 / FFMA2, two elements per instruction); only quarters that
 //     contain a segment start take a branch (SpTTM, whose fibres are mostly
 //     one or two nonzeros long, takes predicated stores instead);
-//   * every 32 nonzeros the stage sum is folded into the segment sum with
-//     Kahan compensation in shared memory, so the error of a long (Zipf-hot)
-//     segment grows with its number of stages, not nonzeros; a segment that
-//     starts and ends between two folds never leaves registers;
+//   * at the end of every stage of 32 nonzeros that holds no segment start,
+//     the register sum is folded into the segment sum with Kahan compensation
+//     in shared memory, so the error of a long (Zipf-hot) segment grows with
+//     its number of stages, not nonzeros, and no register sum spans more than
+//     two stages; a segment that starts and ends between two folds never
+//     leaves registers (short segments, such as SpTTM's fibres of one or two
+//     nonzeros, are stored straight from registers);
 //   * a segment that starts and ends inside a run is stored directly (one
 //     FP32 row per segment); segments cut by run boundaries are combined per
 //     CTA in shared memory (FP64, run order); segments cut by CTA boundaries
@@ -220,13 +223,18 @@ __device__ __forceinline__ bool head_at(const StreamParams &p, int64_t pos) {
 // and the per-group region stride (16 mod 128 so groups hit different banks).
 // After its run a group reuses its region for the FP64 partial of its last
 // segment (rt columns), so the region holds whichever is larger.
-__host__ __device__ constexpr int slot_bytes(int nstream) { return nstream * T * 4 + 16; }
-__host__ __device__ constexpr int group_stride(int nstream, int rt) {
-    return (((NS * slot_bytes(nstream) > rt * 8 ? NS * slot_bytes(nstream) : rt * 8) + 127) / 128) * 128 + 16;
+// nstream arrays, of which the first nidx are index streams of ix bytes per
+// nonzero (4, or 2 after index compression) and the others 4-byte streams.
+__host__ __device__ constexpr int slot_bytes(int nstream, int nidx = 0, int ix = 4) {
+    return nidx * T * ix + (nstream - nidx) * T * 4 + 16;
+}
+__host__ __device__ constexpr int group_stride(int nstream, int rt, int nidx = 0, int ix = 4) {
+    return (((NS * slot_bytes(nstream, nidx, ix) > rt * 8 ? NS * slot_bytes(nstream, nidx, ix) : rt * 8) + 127) /
+            128) * 128 + 16;
 }
 // Bytes of dynamic shared memory of one CTA of the streaming kernel.
-__host__ __device__ constexpr size_t stream_smem_bytes(int nstream, int G, int RT) {
-    return (size_t)G * group_stride(nstream, RT)  // stream rings / last-segment partials
+__host__ __device__ constexpr size_t stream_smem_bytes(int nstream, int G, int RT, int nidx = 0, int ix = 4) {
+    return (size_t)G * group_stride(nstream, RT, nidx, ix)  // stream rings / last-segment partials
            + (size_t)G * RT * 8                   // first-segment partials (FP64)
            + (size_t)2 * G * 8 + (size_t)2 * G * 4 + (size_t)G * 4  // segment ids, flags, loss
            + (size_t)G * 2 * RT * 4;              // Kahan sums and compensations
@@ -324,16 +332,29 @@ constexpr int stream_min_blocks() {
     return stream_three_ctas<E, NCH, NP, KIND>() ? 3 : 2;
 }
 
-template <typename TF, int E, int LPR, int NCH, int NP, int KIND>
+// IX: bytes per product-mode index in the stage (4, or 2 for the 16-bit
+// streams of a compressed handle: value kind with one or two product modes).
+template <typename TF, int E, int LPR, int NCH, int NP, int KIND, int IX = 4>
 __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>()) k_stream(const StreamParams p) {
+    static_assert(IX == 4 || (KIND == 0 && (NP == 1 || NP == 2)), "16-bit indices: value kind, 1 or 2 product modes");
     using IO = RowIO<TF, E>;
     using raw = typename IO::raw;
     constexpr int G = kThreads / LPR;  // groups per CTA
     constexpr int RT = NCH * LPR * E;  // columns covered by a group
     const int nprod = NP > 0 ? NP : p.nprod;
-    // stage layout: the product-mode index streams, the values and, for the
-    // residual kind, the permutation to the caller's COO order (for dvals)
+    // stage layout: the product-mode index streams (IX bytes per nonzero),
+    // the values and, for the residual kind, the permutation to the caller's
+    // COO order (for dvals), then the bit-flag word
     const int nstream = nprod + 1 + (KIND == 1 ? 1 : 0);
+    const int val_off = nprod * T * IX;  // byte offset of the values in a slot
+    const int flag_off = val_off + (nstream - nprod) * T * 4;
+    // index u of product-mode stream a, and value u, of a slot
+    auto idx_at = [&](const unsigned char *slot, int a, int u) -> uint32_t {
+        if constexpr (IX == 4)
+            return reinterpret_cast<const uint32_t *>(slot + a * T * 4)[u];
+        else
+            return reinterpret_cast<const uint16_t *>(slot + a * T * 2)[u];
+    };
     const int R = p.R;
     const int tid = threadIdx.x, lane = tid & 31;
     const int g = tid / LPR, lig = tid % LPR;
@@ -341,8 +362,8 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
     const bool has_out = p.out != nullptr;
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const int sbytes = slot_bytes(nstream);
-    const int gstride = group_stride(nstream, RT);
+    const int sbytes = slot_bytes(nstream, nprod, IX);
+    const int gstride = group_stride(nstream, RT, nprod, IX);
     unsigned char *ring = smem + (size_t)g * gstride;
     double *s_first = reinterpret_cast<double *>(smem + (size_t)G * gstride);  // [G][RT]
     int64_t *s_pseg = reinterpret_cast<int64_t *>(s_first + (size_t)G * RT);
@@ -413,8 +434,21 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
             if (s < nst) {
                 const int64_t base = r0 + (int64_t)s * T;
                 unsigned char *slot = ring + (s % NS) * sbytes;
-                constexpr int CPA = T / 4;  // 16-byte pieces per stream array
-                if constexpr (NP > 0 && LPR <= CPA) {
+                constexpr int CPA = T / 4;  // 16-byte pieces per 4-byte stream array
+                if constexpr (IX == 2) {
+                    // NP 16-bit index arrays (T * 2 bytes each), then the values
+                    constexpr int CPI = T * 2 / 16;
+#pragma unroll
+                    for (int c = lig; c < NP * CPI + CPA; c += LPR) {
+                        if (c < NP * CPI) {
+                            const int a = c / CPI, q = c % CPI;
+                            cp_async16(slot + a * T * 2 + q * 16, p.pidx16[a] + base + q * 8);
+                        } else {
+                            const int q = c - NP * CPI;
+                            cp_async16(slot + val_off + q * 16, p.val + base + q * 4);
+                        }
+                    }
+                } else if constexpr (NP > 0 && LPR <= CPA) {
                     // piece i * LPR + lig: the array is the same for every lane
 #pragma unroll
                     for (int i = 0; i < (NP + 1 + (KIND == 1 ? 1 : 0)) * CPA / LPR; ++i) {
@@ -436,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                         cp_async16(slot + a * T * 4 + q * 16, src);
                     }
                 }
-                if (lig == 0) cp_async4(slot + nstream * T * 4, p.bf + (base >> 5));
+                if (lig == 0) cp_async4(slot + flag_off, p.bf + (base >> 5));
             }
             cp_async_commit();
         };
@@ -602,7 +636,8 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                         const float2 v2 = make_float2(v, v);
 #pragma unroll
                         for (int e = 0; e < E; e += 2) {
-                            const float2 s = __fmul2_rn(v2, make_float2(brow[c][e], brow[c][e + 1]));
+                            // one product mode: there is no other row to multiply (brow = 1)
+                            const float2 s = NP == 1 ? v2 : __fmul2_rn(v2, make_float2(brow[c][e], brow[c][e + 1]));
                             const float2 a = __ffma2_rn(s, make_float2(t[c][e], t[c][e + 1]),
                                                         make_float2(acc_st[c][e], acc_st[c][e + 1]));
                             acc_st[c][e] = a.x;
@@ -654,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                         // in F-COO order, or the caller's COO order through the streamed permutation
                         const int64_t at = p.dvals_fcoo ? base + u
                                                         : (int64_t)reinterpret_cast<const uint32_t *>(
-                                                              slot + (nprod + 1) * T * 4)[u];
+                                                              slot + val_off + T * 4)[u];
                         p.dvals[at] = p.dsign * w;
                     }
                 }
@@ -674,7 +709,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                     float b = 1.f;
                     for (int m = nprod - 2; m >= 0; --m) {
                         const TF *Fm = static_cast<const TF *>(p.F[m]);
-                        const uint32_t km = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[u];
+                        const uint32_t km = idx_at(slot, m, u);
                         b *= ld_elem(Fm + (size_t)km * Rin + q % Rin);
                         q /= Rin;
                     }
@@ -688,7 +723,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                 for (int e = 0; e < E; ++e) brow[c][e] = 1.f;
                 for (int m = 0; m < nprod - 1; ++m) {
                     const TF *Fm = static_cast<const TF *>(p.F[m]);
-                    const uint32_t km = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[u];
+                    const uint32_t km = idx_at(slot, m, u);
                     float t[E];
                     IO::cvt(IO::load(Fm + (size_t)km * R + colc[c]), t);
 #pragma unroll
@@ -738,26 +773,37 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         auto prefetch = [&](Quarter &b, const unsigned char *slot, int qt, uint32_t hw) {
             const int ub = qt * Q;
             uint32_t kk[Q], jj[Q];
+            // Q consecutive indices of product-mode stream a
+            auto idx_q = [&](int a, uint32_t (&o)[Q]) {
+                if constexpr (IX == 4) {
+                    if constexpr (Q == 4) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(slot + a * T * 4 + ub * 4);
+                        o[0] = w.x, o[1] = w.y, o[2] = w.z, o[3] = w.w;
+                    } else {
+                        const uint2 w = *reinterpret_cast<const uint2 *>(slot + a * T * 4 + ub * 4);
+                        o[0] = w.x, o[1] = w.y;
+                    }
+                } else {  // two 16-bit indices per word, the lower position in the low half
+                    if constexpr (Q == 4) {
+                        const uint2 w = *reinterpret_cast<const uint2 *>(slot + a * T * 2 + ub * 2);
+                        o[0] = w.x & 0xffffu, o[1] = w.x >> 16, o[2] = w.y & 0xffffu, o[3] = w.y >> 16;
+                    } else {
+                        const uint32_t w = *reinterpret_cast<const uint32_t *>(slot + a * T * 2 + ub * 2);
+                        o[0] = w & 0xffffu, o[1] = w >> 16;
+                    }
+                }
+            };
+            idx_q(nprod - 1, kk);
             if constexpr (Q == 4) {
-                const uint4 k4 = *reinterpret_cast<const uint4 *>(slot + (nprod - 1) * T * 4 + ub * 4);
-                const float4 v4 = *reinterpret_cast<const float4 *>(slot + nprod * T * 4 + ub * 4);
-                kk[0] = k4.x, kk[1] = k4.y, kk[2] = k4.z, kk[3] = k4.w;
+                const float4 v4 = *reinterpret_cast<const float4 *>(slot + val_off + ub * 4);
                 b.vv[0] = v4.x, b.vv[1] = v4.y, b.vv[2] = v4.z, b.vv[3] = v4.w;
             } else {
-                const uint2 k2 = *reinterpret_cast<const uint2 *>(slot + (nprod - 1) * T * 4 + ub * 4);
-                const float2 v2 = *reinterpret_cast<const float2 *>(slot + nprod * T * 4 + ub * 4);
-                kk[0] = k2.x, kk[1] = k2.y;
+                const float2 v2 = *reinterpret_cast<const float2 *>(slot + val_off + ub * 4);
                 b.vv[0] = v2.x, b.vv[1] = v2.y;
             }
             uint32_t fcm = (hw >> ub) & ((1u << Q) - 1u);
             if constexpr (NP == 2) {
-                if constexpr (Q == 4) {
-                    const uint4 j4 = *reinterpret_cast<const uint4 *>(slot + ub * 4);
-                    jj[0] = j4.x, jj[1] = j4.y, jj[2] = j4.z, jj[3] = j4.w;
-                } else {
-                    const uint2 j2 = *reinterpret_cast<const uint2 *>(slot + ub * 4);
-                    jj[0] = j2.x, jj[1] = j2.y;
-                }
+                idx_q(0, jj);
 #pragma unroll
                 for (int q = 0; q < Q; ++q) fcm |= (uint32_t)(jj[q] != (q ? jj[q - 1] : jprev)) << q;
                 jprev = jj[Q - 1];
@@ -765,7 +811,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                 for (int q = 0; q < Q; ++q) {
                     bool ch = false;
                     for (int m = 0; m < nprod - 1; ++m) {
-                        const uint32_t k = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[ub + q];
+                        const uint32_t k = idx_at(slot, m, ub + q);
                         ch |= k != lastkey[m];
                         lastkey[m] = k;
                     }
@@ -801,7 +847,11 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         };
         // consume quarter qt (hdm = its segment-start bits)
         auto consume = [&](const Quarter &b, const unsigned char *slot, int qt, uint32_t hdm, int64_t base) {
-            if (hdm == 0) {
+            // SpTTM (one product mode, value weights, rows = segments): the
+            // quarters of all groups take the same predicated path whether or
+            // not they hold a segment start, so a warp does not split on them
+            const bool short_path = NP == 1 && KIND == 0 && !p.segrow && has_out && !first && !in_smem;
+            if (hdm == 0 && !short_path) {
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const bool f = (b.fcm >> q) & 1u;
@@ -821,7 +871,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                     }
                     accumulate(b.vv[q], b.cr[q], slot, base, qt * Q + q);
                 }
-            } else if (NP == 1 && KIND == 0 && !p.segrow && has_out && !first && !in_smem) {
+            } else if (short_path) {
                 // SpTTM: fibres of one or two nonzeros are the norm, so segment
                 // starts take predicated stores and selects instead of a branch
                 // per nonzero (a warp's groups would diverge on almost every
@@ -829,19 +879,25 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                 // (folds happen at stage ends), so the test is made once per
                 // quarter; a run's first segment and segments that reached a
                 // fold take the general path.
+                // the lane's first column of the current output row, stepped
+                // by one multiply-add per nonzero
+                char *ocol = reinterpret_cast<char *>(orow + col[0]);
+                const uint32_t rbytes = (uint32_t)R * 4u;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const bool hd = (hdm >> q) & 1u;
+                    const uint32_t hd = (hdm >> q) & 1u;
 #pragma unroll
                     for (int c = 0; c < NCH; ++c) {
-                        if (hd && act[c]) store_row<E>(orow + col[c], acc_st[c]);
+                        if (hd && act[c])
+                            store_row<E>(reinterpret_cast<float *>(ocol) + (col[c] - col[0]), acc_st[c]);
 #pragma unroll
                         for (int e = 0; e < E; ++e) acc_st[c][e] = hd ? 0.f : acc_st[c][e];
                     }
-                    orow += hd ? R : 0;
+                    ocol += (uint64_t)(hd * rbytes);
                     accumulate(b.vv[q], b.cr[q], slot, base, qt * Q + q);
                 }
                 const int nh = __popc(hdm);
+                orow += (int64_t)nh * R;
                 seg += nh;
                 row += nh;
             } else {
@@ -865,18 +921,18 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         };
         // ragged last stage: nonzeros one at a time, no pipelining
         auto process_tail = [&](const unsigned char *slot, int64_t base, uint32_t hw, int cnt) {
-            const uint32_t *sk = reinterpret_cast<const uint32_t *>(slot + (nprod - 1) * T * 4);
-            const uint32_t *sj = reinterpret_cast<const uint32_t *>(slot);
-            const float *sv = reinterpret_cast<const float *>(slot + nprod * T * 4);
+            const float *sv = reinterpret_cast<const float *>(slot + val_off);
             for (int u = 0; u < cnt; ++u) {
                 const bool hd = (hw >> u) & 1u;
                 bool f = hd;
+                const uint32_t sku = idx_at(slot, nprod - 1, u);
+                const uint32_t sju = NP == 2 ? idx_at(slot, 0, u) : 0u;
                 if constexpr (NP == 2) {
-                    f |= sj[u] != jprev;
-                    jprev = sj[u];
+                    f |= sju != jprev;
+                    jprev = sju;
                 } else if constexpr (NP != 1) {
                     for (int m = 0; m < nprod - 1; ++m) {
-                        const uint32_t k = reinterpret_cast<const uint32_t *>(slot + m * T * 4)[u];
+                        const uint32_t k = idx_at(slot, m, u);
                         f |= k != lastkey[m];
                         lastkey[m] = k;
                     }
@@ -884,17 +940,17 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                 raw cr[NCL];
 #pragma unroll
                 for (int c = 0; c < NCL; ++c)
-                    cr[c] = IO::load(reinterpret_cast<const TF *>(Flb[c] + (uint64_t)sk[u] * Rb));
+                    cr[c] = IO::load(reinterpret_cast<const TF *>(Flb[c] + (uint64_t)sku * Rb));
                 if (hd) new_segment();
                 if (f) {
                     if constexpr (NP == 2 && KIND == 2) {
 #pragma unroll
                         for (int c = 0; c < NCH; ++c)
-                            brow[c][0] = ld_elem(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sj[u] * Rb));
+                            brow[c][0] = ld_elem(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sju * Rb));
                     } else if constexpr (NP == 2) {
 #pragma unroll
                         for (int c = 0; c < NCH; ++c)
-                            IO::cvt(IO::load(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sj[u] * Rb)), brow[c]);
+                            IO::cvt(IO::load(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sju * Rb)), brow[c]);
                     } else if constexpr (NP != 1) {
                         set_brow_sync(slot, u);
                     }
@@ -914,7 +970,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
             const unsigned char *slot = ring + (s % NS) * sbytes;
             const int64_t base = r0 + (int64_t)s * T;
             const int cnt = (int)min((int64_t)T, r1 - base);
-            uint32_t hw = *reinterpret_cast<const uint32_t *>(slot + nstream * T * 4);
+            uint32_t hw = *reinterpret_cast<const uint32_t *>(slot + flag_off);
             if (s == 0) hw &= ~1u;  // r0 opens the run, not a new segment
             if (PIPE && cnt == T) {
                 if (!have_first) prefetch(qa, slot, 0, hw);
@@ -932,7 +988,7 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                         cp_async_wait<NS - 2>();
                         __syncwarp(gmask);
                         const unsigned char *nslot = ring + ((s + 1) % NS) * sbytes;
-                        prefetch(qa, nslot, 0, *reinterpret_cast<const uint32_t *>(nslot + nstream * T * 4));
+                        prefetch(qa, nslot, 0, *reinterpret_cast<const uint32_t *>(nslot + flag_off));
                         have_first = true;
                     }
                     consume(qb, slot, qt + 1, (hw >> ((qt + 1) * Q)) & ((1u << Q) - 1u), base);
@@ -940,7 +996,12 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
             } else {
                 process_tail(slot, base, hw, cnt);
             }
-            fold();  // stage sums folded every 32 nonzeros
+            // fold where no segment started in this stage: the open segment
+            // then began before it, so its register sum holds at most two
+            // stages' terms; a segment that started here stays in registers
+            // (it has at most 32 terms), which keeps short segments off the
+            // folded path
+            if ((hw & (cnt == T ? kFull : (1u << cnt) - 1u)) == 0u) fold();
         }
         // ---- end of run: the last segment (its partial may go to the ring
         // region, so every lane of the group must be done with the ring)
@@ -1066,15 +1127,15 @@ __global__ void __launch_bounds__(256) k_carry_fixup(const StreamParams p) {
 
 // ------------------------------------------------------------ launch
 
-template <typename TF, int E, int LPR, int NCH, int NP, int KIND>
+template <typename TF, int E, int LPR, int NCH, int NP, int KIND, int IX = 4>
 int launch_variant(StreamParams &p, cudaStream_t s) {
     constexpr int G = kThreads / LPR;
     constexpr int RT = NCH * LPR * E;
-    auto kern = k_stream<TF, E, LPR, NCH, NP, KIND>;
+    auto kern = k_stream<TF, E, LPR, NCH, NP, KIND, IX>;
     // the shared memory size depends on the number of streams, which the
     // general-N variant (NP = 0) takes at run time: one cache per size
     const int nstream = p.nprod + 1 + (KIND == 1 ? 1 : 0);
-    const size_t smem = stream_smem_bytes(nstream, G, RT);
+    const size_t smem = stream_smem_bytes(nstream, G, RT, p.nprod, IX);
     int dev = 0, occ = 0;
     FCOO_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(FCOO_ERR_UNSUPPORTED, "device %d above %d", dev, kMaxDevices);
@@ -1117,11 +1178,20 @@ int launch_variant(StreamParams &p, cudaStream_t s) {
 
 template <typename TF, int E, int LPR, int NCH, int KIND>
 int launch_np(StreamParams &p, cudaStream_t s) {
+    // a compressed handle's 16-bit index streams serve the value kind with
+    // one or two product modes
+    const bool ix16 = KIND == 0 && p.pidx16[0] != nullptr;
     switch (p.nprod) {
         case 1:
-            if constexpr (KIND == 0) return launch_variant<TF, E, LPR, NCH, 1, KIND>(p, s);
+            if constexpr (KIND == 0) {
+                if (ix16) return launch_variant<TF, E, LPR, NCH, 1, KIND, 2>(p, s);
+                return launch_variant<TF, E, LPR, NCH, 1, KIND>(p, s);
+            }
             return launch_variant<TF, E, LPR, NCH, 0, KIND>(p, s);
-        case 2: return launch_variant<TF, E, LPR, NCH, 2, KIND>(p, s);
+        case 2:
+            if constexpr (KIND == 0)
+                if (ix16) return launch_variant<TF, E, LPR, NCH, 2, KIND, 2>(p, s);
+            return launch_variant<TF, E, LPR, NCH, 2, KIND>(p, s);
         default: return launch_variant<TF, E, LPR, NCH, 0, KIND>(p, s);
     }
 }

@@ -38,6 +38,9 @@ def test_table2_bytes_golden(fc):
         assert fc.table2_bytes(1, row["nnz"], row["threadlen"]) == row["fcoo_ttm"]
         assert fc.table2_bytes(2, row["nnz"], row["threadlen"]) == row["fcoo_mttkrp"]
         assert row["fcoo_mttkrp"] < row["coo"]
+        assert fc.table2_bytes(1, row["nnz"], row["threadlen"], index_bytes=2) == row["fcoo_ttm_idx16"]
+        assert fc.table2_bytes(2, row["nnz"], row["threadlen"], index_bytes=2) == row["fcoo_mttkrp_idx16"]
+    assert fc.table2_bytes(2, 1000, 8, index_bytes=3) == -1
     assert fc.table2_bytes(2, 1000, 7) == -1
     assert fc.table2_bytes(2, 1000, 128) == -1
     assert fc.table2_bytes(0, 1000, 8) == -1
