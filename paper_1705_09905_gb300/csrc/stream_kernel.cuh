@@ -80,8 +80,16 @@ template <>
 struct RowIO<float, 4> {
     using raw = float4;
     static __device__ __forceinline__ raw load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-    static __device__ __forceinline__ raw zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-    static __device__ __forceinline__ raw load_if(const float *p, bool f) { return f ? load(p) : zero(); }
+    // as RowIO<float, 8>::load_if: unspecified where f is false
+    static __device__ __forceinline__ raw load_if(const float *p, bool f) {
+        raw r;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
+            "@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];\n\t}"
+            : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+            : "l"(p), "r"((unsigned)f));
+        return r;
+    }
     static __device__ __forceinline__ void cvt(const raw &r, float (&v)[4]) {
         v[0] = r.x;
         v[1] = r.y;
@@ -105,20 +113,15 @@ struct RowIO<float, 8> {
             : "l"(p));
         return r;
     }
-    static __device__ __forceinline__ raw zero() {
-        raw r;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) r.v[i] = 0.f;
-        return r;
-    }
-    // the load only where f holds (zeros elsewhere), as one predicated instruction
+    // the load only where f holds, as one predicated instruction; where f is
+    // false the result is unspecified (callers select it away)
     static __device__ __forceinline__ raw load_if(const float *p, bool f) {
-        raw r = zero();
+        raw r;
         asm volatile(
             "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %9, 0;\n\t"
             "@q ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t}"
-            : "+f"(r.v[0]), "+f"(r.v[1]), "+f"(r.v[2]), "+f"(r.v[3]), "+f"(r.v[4]), "+f"(r.v[5]), "+f"(r.v[6]),
-              "+f"(r.v[7])
+            : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]), "=f"(r.v[4]), "=f"(r.v[5]), "=f"(r.v[6]),
+              "=f"(r.v[7])
             : "l"(p), "r"((unsigned)f));
         return r;
     }
@@ -134,8 +137,16 @@ struct RowIO<__nv_bfloat16, 8> {
     static __device__ __forceinline__ raw load(const __nv_bfloat16 *p) {
         return __ldg(reinterpret_cast<const uint4 *>(p));
     }
-    static __device__ __forceinline__ raw zero() { return make_uint4(0u, 0u, 0u, 0u); }
-    static __device__ __forceinline__ raw load_if(const __nv_bfloat16 *p, bool f) { return f ? load(p) : zero(); }
+    // as RowIO<float, 8>::load_if: unspecified where f is false
+    static __device__ __forceinline__ raw load_if(const __nv_bfloat16 *p, bool f) {
+        raw r;
+        asm volatile(
+            "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t"
+            "@q ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+            : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+            : "l"(p), "r"((unsigned)f));
+        return r;
+    }
     static __device__ __forceinline__ void cvt(const raw &r, float (&v)[8]) {
         const uint32_t w[4] = {r.x, r.y, r.z, r.w};
 #pragma unroll
