@@ -324,6 +324,44 @@ def time_spmttkrp(fc, Xs, F, outs, steps, warmup, stream):
     return total, per_mode
 
 
+def time_gather_bound(fc, Xs, F, steps, stream):
+    """spmttkrp_gather_bound on each mode: the factor-row loads of spmttkrp
+    alone (no products, reduction or output).  Returns (per-mode mean call
+    seconds, rows loaded per mode)."""
+    cnt = [torch.zeros(1, dtype=torch.int64, device=F[0].device) for _ in range(3)]
+    for _ in range(3):
+        for n in range(3):
+            fc.spmttkrp_gather_bound(Xs[n], F, count=cnt[n], stream=stream)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps * 3)]
+    for s in range(steps):
+        for n in range(3):
+            e = ev[s * 3 + n]
+            e[0].record(stream)
+            fc.spmttkrp_gather_bound(Xs[n], F, count=cnt[n], stream=stream)
+            e[1].record(stream)
+    torch.cuda.synchronize()
+    per_mode = [statistics.mean(ev[s * 3 + n][0].elapsed_time(ev[s * 3 + n][1]) for s in range(steps)) / 1e3
+                for n in range(3)]
+    return per_mode, [int(c.item()) for c in cnt]
+
+
+def gather_bound_record(fc, Xs, F, per_mode, nnz, sm_mhz, sms, stream, steps=20):
+    """The gather-only bound beside the full kernel's per-mode times: the
+    fraction of it that spmttkrp reaches, and both rates in factor rows per
+    SM clock."""
+    gb, rows = time_gather_bound(fc, Xs, F, steps, stream)
+    clk = (sm_mhz or 2070.0) * 1e6
+    return {"ms_per_mode": [t * 1e3 for t in gb], "kernel_ms_per_mode": [t * 1e3 for t in per_mode],
+            "rows_per_mode": rows, "rows_per_nnz": [x / nnz for x in rows],
+            "frac": sum(gb) / sum(per_mode), "frac_per_mode": [a / b for a, b in zip(gb, per_mode)],
+            "rows_per_sm_clk_bound": [x / (t * sms * clk) for x, t in zip(rows, gb)],
+            "rows_per_sm_clk_kernel": [x / (t * sms * clk) for x, t in zip(rows, per_mode)],
+            "source": "spmttkrp_gather_bound: the factor-row loads of spmttkrp on the same handles and "
+                      "factors (C row per nonzero, B row where the fibre or segment changes), same lane "
+                      "layout, nothing else; CUDA events, mean of 20 calls per mode"}
+
+
 def e2e_spmttkrp(fc, Xs, dims, R, steps, stream):
     """Through the public API with host buffers: upload the factors from pinned
     host memory, three SpMTTKRP calls, download the three results, per step."""
@@ -547,9 +585,11 @@ def bench_mttkrp_bf16(fc, Xs, dims, R, steps=50):
     outs = [torch.empty((dims[n], R), device=dev) for n in range(3)]
     total, per_mode = time_spmttkrp(fc, Xs, F, outs, steps, 5, torch.cuda.current_stream())
     alg = [mttkrp_alg_bytes(Xs[n], R, 2) for n in range(3)]
+    gb, _ = time_gather_bound(fc, Xs, F, 20, torch.cuda.current_stream())
     return {"R": R, "factors": "bf16", "ms_per_step": total / steps * 1e3,
             "GBps": sum(alg) * steps / total / 1e9,
-            "per_mode_ms": [t * 1e3 for t in per_mode]}
+            "per_mode_ms": [t * 1e3 for t in per_mode],
+            "gather_bound_ms_per_mode": [t * 1e3 for t in gb], "frac_of_gather_bound": sum(gb) / sum(per_mode)}
 
 
 def host_cpu_model() -> str:
@@ -785,6 +825,9 @@ def run_ours(args):
                     torch.cuda.get_device_properties(dev).multi_processor_count)
     if g:
         line["roofline"]["gather"] = g
+    line["roofline"]["gather_bound"] = gather_bound_record(
+        fc, Xs, F, per_mode, cfg.nnz, clocks.get("sm_mhz"),
+        torch.cuda.get_device_properties(dev).multi_processor_count, stream)
     if not args.no_extras and rank == 0:
         for name, fn in (("mttkrp_bf16", lambda: bench_mttkrp_bf16(fc, Xs, cfg.dims, R)),
                          ("spttm", lambda: bench_spttm(fc, dev, args.quick)),
@@ -838,7 +881,14 @@ def summarize(line):
         out["spttm_idx16"] = {"ms": r(get(t, "ms")), "GBps": r(get(t, "GBps"), 1), "speedup": r(get(t, "speedup"), 3)}
     if "mttkrp_bf16" in line:
         t = line["mttkrp_bf16"]
-        out["spmttkrp_bf16_R32"] = {"ms_per_step": r(get(t, "ms_per_step")), "GBps": r(get(t, "GBps"), 1)}
+        out["spmttkrp_bf16_R32"] = {"ms_per_step": r(get(t, "ms_per_step")), "GBps": r(get(t, "GBps"), 1),
+                                    "frac_of_gather_bound": r(get(t, "frac_of_gather_bound"))}
+    gbr = get(line, "roofline", "gather_bound")
+    if gbr:
+        out["spmttkrp_fp32_R32_gather_bound"] = {"ms_per_mode": [r(x) for x in gbr["ms_per_mode"]],
+                                                 "frac": r(gbr["frac"]),
+                                                 "rows_per_sm_clk_kernel": [r(x) for x in gbr["rows_per_sm_clk_kernel"]],
+                                                 "rows_per_sm_clk_bound": [r(x) for x in gbr["rows_per_sm_clk_bound"]]}
     if "cp_als" in line:
         c = line["cp_als"]
         out["cp_als_R64_20"] = {

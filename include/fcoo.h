@@ -393,6 +393,30 @@ typedef struct {
 int spmttkrp_noalloc(const fcoo_view_t *view, const void *const *factors, int dtype, int R, float *out,
                      fcoo_stream_t stream);
 
+/* Gather-only bound of SpMTTKRP on a 3-way tensor (Eq. 6; Sec. IV-D reads
+ * the factor rows through the read-only cache).  A measurement aid, not part
+ * of any result: it loads exactly the factor rows that spmttkrp on the same
+ * handle loads, and nothing else -- per nonzero, in F-COO order along each
+ * lane group's range, the row C(k,:) of the last product mode, and the row
+ * B(j,:) of the first product mode where j changes, a segment starts or the
+ * group's range starts -- with eight columns per lane as spmttkrp's R/8-lane
+ * layout, and no products, reduction or output.  Its duration bounds from
+ * below what the gathers alone cost SpMTTKRP on this tensor and these
+ * factors.
+ * Arguments:
+ *   X            handle built with FCOO_OP_MTTKRP on a 3-way tensor
+ *   factors      as spmttkrp (device rows, dtype FCOO_F32 or FCOO_BF16); the
+ *                two product-mode factors must be 32-byte (F32) or 16-byte
+ *                (BF16) aligned
+ *   R            8, 16, 32, 64, 128 or 256
+ *   rows_loaded  device pointer to one 8-byte counter, set to the number of
+ *                rows loaded (C rows plus B rows)
+ * Asynchronous on `stream`.  Errors (before any device work):
+ * FCOO_ERR_INVALID_ARG (NULL or misaligned pointers, wrong op or dtype),
+ * FCOO_ERR_UNSUPPORTED (not 3-way, another R, factor rows not aligned). */
+int spmttkrp_gather_bound(const fcoo_t *X, const void *const *factors, int dtype, int R,
+                          unsigned long long *rows_loaded, fcoo_stream_t stream);
+
 /* ---------------------------------------------------------------------- */
 /* CP-ALS (Algorithm 1; Sec. IV-D "Complete tensor-based algorithms")       */
 /* ---------------------------------------------------------------------- */

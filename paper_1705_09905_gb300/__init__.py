@@ -17,7 +17,7 @@ import torch
 
 from ._lib import FcooError, FcooInfo, check, lib, ptr_array
 
-__all__ = ["FCOO", "FcooError", "spmttkrp", "spttm", "table2_bytes", "MTTKRP", "TTM", "F32", "BF16", "lib"]
+__all__ = ["FCOO", "FcooError", "spmttkrp", "spmttkrp_gather_bound", "spttm", "table2_bytes", "MTTKRP", "TTM", "F32", "BF16", "lib"]
 
 MTTKRP, TTM = 0, 1
 F32, BF16 = 0, 1
@@ -192,6 +192,33 @@ def spmttkrp(X: FCOO, factors: Sequence[Optional[torch.Tensor]], out: Optional[t
     pp, _keep = ptr_array(ptrs)
     check(lib.spmttkrp(X.handle, pp, dt, R, out.data_ptr(), _stream(stream)))
     return out
+
+
+def spmttkrp_gather_bound(X: FCOO, factors: Sequence[Optional[torch.Tensor]], count: Optional[torch.Tensor] = None,
+                          stream=None) -> torch.Tensor:
+    """The factor-row loads of spmttkrp on this 3-way handle and nothing else
+    (a measurement aid for the gather bound of Eq. 6).  Returns a one-element
+    int64 device tensor that receives the number of rows loaded."""
+    if X.op != MTTKRP:
+        raise ValueError("handle was built for SpTTM")
+    ref = factors[X.prod_modes[0]]
+    R = int(ref.shape[1])
+    dt = _dtype_code(ref)
+    ptrs = []
+    for k in range(X.nmodes):
+        if k == X.mode:
+            ptrs.append(None)
+            continue
+        f = factors[k]
+        _check_factor(f, X.dims[k], R, f"factors[{k}]")
+        if f.dtype != ref.dtype:
+            raise TypeError("all factors must share one dtype")
+        ptrs.append(f.data_ptr())
+    if count is None:
+        count = torch.empty(1, dtype=torch.int64, device=ref.device)
+    pp, _keep = ptr_array(ptrs)
+    check(lib.spmttkrp_gather_bound(X.handle, pp, dt, R, count.data_ptr(), _stream(stream)))
+    return count
 
 
 def spttm(X: FCOO, U: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:

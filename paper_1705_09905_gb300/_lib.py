@@ -84,6 +84,7 @@ SIGNATURES = {
     "spttmc_plan_info": (_i, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "spttmc_plan_destroy": (_i, [_vp]),
     "spmttkrp_noalloc": (_i, [ctypes.POINTER(FcooView), _vpp, _i, _i, _vp, _vp]),
+    "spmttkrp_gather_bound": (_i, [_vp, _vpp, _i, _i, _vp, _vp]),
     "cp_state_create": (_i, [_i, _vp, _i, _i, _vpp, _vp, ctypes.POINTER(_vp)]),
     "tucker_state_create": (_i, [_i, _vp, _i, _vpp, _vp, ctypes.POINTER(_vp)]),
     "tucker_state_destroy": (_i, [_vp]),

@@ -185,6 +185,18 @@ __device__ __forceinline__ float ld_elem(const TF *p) {
     return v[0];
 }
 
+// the products of the two BF16 pairs packed in a and b, each exact in FP32
+// (8-bit significands: the 16-bit product fits in 24 bits), by the mixed
+// BF16 x BF16 + FP32 fused multiply-add with a zero addend
+__device__ __forceinline__ float2 bf16_prod2(uint32_t a, uint32_t b) {
+    float2 r;
+    asm("{\n\t.reg .b16 al, ah, bl, bh;\n\tmov.b32 {al, ah}, %2;\n\tmov.b32 {bl, bh}, %3;\n\t"
+        "fma.rn.f32.bf16 %0, al, bl, 0f00000000;\n\tfma.rn.f32.bf16 %1, ah, bh, 0f00000000;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "r"(a), "r"(b));
+    return r;
+}
+
 template <int E>
 __device__ __forceinline__ void store_row(float *dst, const float (&v)[E]) {
     if constexpr (E == 4) {
@@ -508,6 +520,11 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
         // ends between two folds never leaves registers.  brow = product of
         // the current fibre's non-last product-mode rows
         float acc_st[NCH][E], brow[NCH][E];
+        // SpMTTKRP of a 3-way tensor with BF16 rows: the fibre row stays in
+        // its BF16 words, and each nonzero multiplies it into the gathered row
+        // exactly (bf16_prod2) before the FP32 multiply-add with the value
+        constexpr bool RAWB = std::is_same<TF, __nv_bfloat16>::value && KIND == 0 && NP == 2 && E == 8;
+        uint32_t brw[RAWB ? NCH : 1][4];
         float trow[KIND == 1 ? NCH : 1][E];
         float *s_acc = s_seg + (size_t)g * 2 * RT;  // [RT] sum, then [RT] compensation
         float *s_cmp = s_acc + RT;
@@ -519,6 +536,15 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                 acc_st[c][e] = 0.f;
                 brow[c][e] = 1.f;
             }
+#pragma unroll
+        for (int c = 0; c < (RAWB ? NCH : 1); ++c)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) brw[c][i] = 0x3f803f80u;  // BF16 ones
+        auto set_brw = [&](int c, const raw &r) {
+            if constexpr (RAWB) {
+                brw[c][0] = r.x, brw[c][1] = r.y, brw[c][2] = r.z, brw[c][3] = r.w;
+            }
+        };
         auto load_target = [&]() {
             if constexpr (KIND == 1) {
                 const TF *Tm = static_cast<const TF *>(p.T);
@@ -640,7 +666,20 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
             float t[NCL][E];
 #pragma unroll
             for (int c = 0; c < NCL; ++c) IO::cvt(cr[c], t[c]);
-            if constexpr (KIND == 0) {
+            if constexpr (RAWB) {
+                const float2 v2 = make_float2(v, v);
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    const uint32_t cw[4] = {cr[c].x, cr[c].y, cr[c].z, cr[c].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 a = __ffma2_rn(v2, bf16_prod2(brw[c][i], cw[i]),
+                                                    make_float2(acc_st[c][2 * i], acc_st[c][2 * i + 1]));
+                        acc_st[c][2 * i] = a.x;
+                        acc_st[c][2 * i + 1] = a.y;
+                    }
+                }
+            } else if constexpr (KIND == 0) {
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) {
                     if constexpr (E % 2 == 0) {
@@ -869,6 +908,15 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                     if constexpr (NP == 2 && KIND == 2) {
 #pragma unroll
                         for (int c = 0; c < NCH; ++c) brow[c][0] = f ? b.br[q][c] : brow[c][0];
+                    } else if constexpr (RAWB) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c) {
+                            const raw &r = b.br[q][c];
+                            brw[c][0] = f ? r.x : brw[c][0];
+                            brw[c][1] = f ? r.y : brw[c][1];
+                            brw[c][2] = f ? r.z : brw[c][2];
+                            brw[c][3] = f ? r.w : brw[c][3];
+                        }
                     } else if constexpr (NP == 2) {
 #pragma unroll
                         for (int c = 0; c < NCH; ++c) {
@@ -919,6 +967,9 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
                         if constexpr (NP == 2 && KIND == 2) {
 #pragma unroll
                             for (int c = 0; c < NCH; ++c) brow[c][0] = b.br[q][c];
+                        } else if constexpr (RAWB) {
+#pragma unroll
+                            for (int c = 0; c < NCH; ++c) set_brw(c, b.br[q][c]);
                         } else if constexpr (NP == 2) {
 #pragma unroll
                             for (int c = 0; c < NCH; ++c) IO::cvt(b.br[q][c], brow[c]);
@@ -958,6 +1009,10 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
 #pragma unroll
                         for (int c = 0; c < NCH; ++c)
                             brow[c][0] = ld_elem(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sju * Rb));
+                    } else if constexpr (RAWB) {
+#pragma unroll
+                        for (int c = 0; c < NCH; ++c)
+                            set_brw(c, IO::load(reinterpret_cast<const TF *>(Fbb[c] + (uint64_t)sju * Rb)));
                     } else if constexpr (NP == 2) {
 #pragma unroll
                         for (int c = 0; c < NCH; ++c)
