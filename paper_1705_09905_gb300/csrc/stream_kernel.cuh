@@ -797,14 +797,18 @@ __global__ void __launch_bounds__(kThreads, stream_min_blocks<E, NCH, NP, KIND>(
             Fbb[c] = reinterpret_cast<const char *>(Fb + colB[c]);
         }
 
-        // ---- software pipeline over quarters of a stage (Q nonzeros; 4, or 2
-        // when a lane holds more than 4 columns or the variant runs 3 CTAs per
-        // SM): the gathers of quarter h+1
-        // are in flight while quarter h is consumed.  A full stage is walked
-        // by a rolled loop over pairs of quarters (two register buffers); the
-        // first quarter of the next stage is requested while the last quarter
-        // of the current one is consumed.
-        constexpr int Q = (E * NCH <= 4 && !stream_three_ctas<E, NCH, NP, KIND>()) ? 4 : 2;
+        // ---- software pipeline over quarters of a stage (Q nonzeros): the
+        // gathers of quarter h+1 are in flight while quarter h is consumed.  A
+        // full stage is walked by a rolled loop over pairs of quarters (two
+        // register buffers); the first quarter of the next stage is requested
+        // while the last quarter of the current one is consumed.  Q is 4 where
+        // a lane holds at most 4 FP32 columns (2 CTAs per SM) and for the BF16
+        // value pass (eight columns in four registers per row: measured 3.5-5 %
+        // faster SpMTTKRP than Q = 2 at R = 32 and 64, 14 % faster SpTTM at
+        // R = 64); 2 otherwise (FP32 rows of eight columns, whose four-nonzero
+        // quarters spill, and the 3-CTA variant).
+        constexpr bool BF16V = std::is_same<TF, __nv_bfloat16>::value && E == 8 && KIND == 0;
+        constexpr int Q = ((E * NCH <= 4 && !stream_three_ctas<E, NCH, NP, KIND>()) || BF16V) ? 4 : 2;
         constexpr int QPS = T / Q;  // quarters per stage (even)
         static_assert(QPS % 2 == 0, "quarters are consumed in pairs");
         // the unrolled pipeline serves the 3-way SpMTTKRP and SpTTM vector
