@@ -53,6 +53,15 @@ def test_bf16_factors(fc, oracle, R):
     run_mttkrp(fc, oracle, T, R, 1, dtype=torch.bfloat16)
 
 
+@pytest.mark.parametrize("R", [32, 64])
+def test_bf16_skewed_many_ctas(fc, oracle, R):
+    # the BF16 value pass (four-nonzero quarters) over a Zipf tensor large
+    # enough for every CTA, run and stage, with a ragged last stage, all modes
+    T = synth.make_tensor(synth.scaled(synth.CONFIGS["skewed3"], 1_000_003, dims=(3000, 2000, 5000)))
+    for mode in range(3):
+        run_mttkrp(fc, oracle, T, R, mode, dtype=torch.bfloat16, seed=R)
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_4way(fc, oracle, mode):
     T = synth.random_small((30, 20, 25, 15), 9000, seed=7 + mode)
@@ -163,15 +172,17 @@ def test_ttm_4way_zipf(fc, oracle, mode):
 
 
 @pytest.mark.parametrize("R,dtype", [(1, torch.float32), (7, torch.float32), (16, torch.bfloat16),
-                                     (64, torch.float32), (256, torch.float32)])
+                                     (32, torch.bfloat16), (64, torch.bfloat16), (64, torch.float32),
+                                     (256, torch.float32)])
 def test_ttm_ranks(fc, oracle, R, dtype):
     T = synth.random_small((40, 30, 50), 12_000, seed=R)
     run_ttm(fc, oracle, T, R, 2, dtype=dtype)
 
 
-def test_ttm_one_long_fibre(fc, oracle):
+@pytest.mark.parametrize("R,dtype", [(16, torch.float32), (64, torch.bfloat16)])
+def test_ttm_one_long_fibre(fc, oracle, R, dtype):
     n = 200_000
     k = np.random.default_rng(1).choice(1_000_000, size=n, replace=False)
     T = synth.SparseTensor((3, 4, 1_000_000), [torch.full((n,), 2), torch.full((n,), 3), torch.as_tensor(k)],
                            torch.rand(n, generator=torch.Generator().manual_seed(2)))
-    run_ttm(fc, oracle, T, 16, 2)
+    run_ttm(fc, oracle, T, R, 2, dtype=dtype)
