@@ -828,6 +828,15 @@ def run_ours(args):
     line["roofline"]["gather_bound"] = gather_bound_record(
         fc, Xs, F, per_mode, cfg.nnz, clocks.get("sm_mhz"),
         torch.cuda.get_device_properties(dev).multi_processor_count, stream)
+    # which roof binds: the L2-served factor-row gathers, not HBM (whose
+    # fraction is the `frac` above) and not the L1 data path or L2 throughput
+    gbr = line["roofline"]["gather_bound"]
+    l2f = (g or {}).get("l2_frac")
+    line["roofline"]["binding"] = (
+        f"factor-row gathers served from L2, at the rows in flight the register file holds: the kernel takes "
+        f"{1 / gbr['frac']:.2f}x the time of its row loads alone (gather_bound); HBM at {achieved / hbm:.1%}"
+        + (f", L2 at {l2f:.0%} and the L1 data path at {g['frac']:.0%} of their peaks" if g and l2f else "")
+        + " are not saturated")
     if not args.no_extras and rank == 0:
         for name, fn in (("mttkrp_bf16", lambda: bench_mttkrp_bf16(fc, Xs, cfg.dims, R)),
                          ("spttm", lambda: bench_spttm(fc, dev, args.quick)),
@@ -883,6 +892,8 @@ def summarize(line):
         t = line["mttkrp_bf16"]
         out["spmttkrp_bf16_R32"] = {"ms_per_step": r(get(t, "ms_per_step")), "GBps": r(get(t, "GBps"), 1),
                                     "frac_of_gather_bound": r(get(t, "frac_of_gather_bound"))}
+    if get(line, "roofline", "binding"):
+        out["binding_roof"] = get(line, "roofline", "binding")
     gbr = get(line, "roofline", "gather_bound")
     if gbr:
         out["spmttkrp_fp32_R32_gather_bound"] = {"ms_per_mode": [r(x) for x in gbr["ms_per_mode"]],
