@@ -854,7 +854,10 @@ def run_ours(args):
                 line[name] = {"error": f"{type(e).__name__}: {e}"}
             torch.cuda.synchronize()
     if not args.no_extras and rank == 0:
-        line["summary"] = summarize(line)  # last: the part of the line a short tail shows
+        try:  # last: the part of the line a short tail shows
+            line["summary"] = summarize(line)
+        except Exception as e:  # the line is printed whatever the summary does
+            line["summary"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg is not None:
