@@ -973,8 +973,11 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=40_000_000)
     ap.add_argument("--cpu-sample-single", type=int, default=4_000_000)
     ap.add_argument("--ref-sample", type=int, default=2_000_000)
-    ap.add_argument("--part", default="all", choices=["all", "spttm", "spttmc", "tucker", "cp", "fit", "sweep"],
+    ap.add_argument("--part", default="all",
+                    choices=["all", "spttm", "spttmc", "tucker", "cp", "fit", "sweep", "bf16"],
                     help="only one extra line, for profiling: spttm (4-way workload, --nnz scales it), "
+                         "bf16 (SpMTTKRP of the skewed 3-way workload with BF16 factors, --nnz and --rank "
+                         "scale it), "
                          "spttmc (SpTTMc of every mode of the skewed 3-way workload, R = 8 and 16), "
                          "tucker (HOOI at R = 8 on the skewed 3-way workload), "
                          "cp (CP-ALS on the skewed 3-way workload), fit (sparse CP fit) or sweep "
@@ -989,6 +992,11 @@ def main():
             line = bench_spttm(fc, dev, args.quick, args.nnz)
         elif args.part == "fit":
             line = bench_sparse_fit(fc, dev, args.quick)
+        elif args.part == "bf16":
+            cfg = workload_config(args)
+            _, Xs, _, _ = build_workload(cfg, dev)
+            line = bench_mttkrp_bf16(fc, Xs, cfg.dims, cfg.R)
+            line["workload"] = cfg.note
         elif args.part == "sweep":
             line = bench_sweep(fc, dev, args.quick)
         elif args.part == "tucker":
